@@ -1,0 +1,132 @@
+/*
+ * gwchi -- imaginary-time polarizability chi_PQ(i tau) of the low-scaling GW
+ * method in a Gaussian basis with resolution of the identity in the overlap
+ * metric (Wilhelm, Golze, Talirz, Hutter, Pignedoli, arXiv 2104.09857),
+ * computed on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every call returns GW_OK (0) or a negative GW_ERR_* code; the text of
+ * the last error of a context is available from gw_last_error().  All device
+ * work of a context runs on the CUDA stream given to gw_create (or a stream the
+ * library creates).  Host arrays passed in are copied before the call returns;
+ * the library never keeps or frees caller memory.
+ *
+ * Units: distances in Angstrom, energies in Hartree, imaginary time in a.u.
+ * Layouts are row-major.  Atom-blocked basis: atom a owns n_ao[a] consecutive
+ * primary (AO) functions and n_ri[a] consecutive auxiliary (RI) functions, in
+ * atom order.
+ */
+#ifndef GWCHI_H
+#define GWCHI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_ctx gw_ctx;
+
+enum gw_status {
+  GW_OK = 0,
+  GW_ERR_INVALID_ARG = -1, /* bad size, null pointer, out-of-range index     */
+  GW_ERR_ORDER = -2,       /* a prerequisite set_* call is missing          */
+  GW_ERR_ASYM = -3,        /* an (A, A, P) 3c block is not symmetric        */
+  GW_ERR_NONFINITE = -4,   /* NaN or Inf in an input                         */
+  GW_ERR_OOM = -5,         /* device allocation failed                       */
+  GW_ERR_CUDA = -6,        /* a CUDA runtime call or kernel failed           */
+  GW_ERR_TIMEOUT = -7,     /* a bounded device wait gave up                  */
+  GW_ERR_NOT_SPD = -8,     /* a Cholesky factorisation met a non-positive pivot */
+  GW_ERR_UNSUPPORTED = -9  /* option not available in this build             */
+};
+
+/* Arithmetic of the contraction steps (Eq. 3).  Green's functions are always
+ * built in FP64; chi is always accumulated across blocks in FP64. */
+enum gw_precision {
+  GW_FP64 = 0,   /* FP64 operands, FP64 accumulation (CUDA cores)                  */
+  GW_FP32 = 1,   /* FP32 operands, FP32 accumulation per block slab (CUDA cores)   */
+  GW_BF16X3 = 2, /* two-term BF16 split, 3 products per product, FP32 accumulation
+                    on the tensor cores (tcgen05)                                  */
+  GW_BF16X6 = 3  /* three-term BF16 split, 6 products per product, FP32
+                    accumulation on the tensor cores (tcgen05)                     */
+};
+
+enum gw_screening {
+  GW_SCREEN_BOUND = 0, /* exact block filter of the paper (norm < thr dropped)    */
+  GW_SCREEN_MLP = 1    /* additionally skip work a learned norm model predicts to
+                          fall below thr                                          */
+};
+
+typedef struct gw_stats {
+  double flops_useful;   /* 2*n*m*k summed over the surviving atom-block products
+                            of steps A, B and C (padding and split products not
+                            counted)                                              */
+  double flops_a, flops_b, flops_c;  /* the same, per step                       */
+  double flops_issued;   /* arithmetic the kernels actually issued (padded tiles,
+                            all split products)                                   */
+  double ms_greens, ms_step_ab, ms_filter, ms_step_c, ms_total; /* last chi call */
+  double ms_step_c_kernel; /* device time of the step-C kernels alone           */
+  long long c_launches;  /* step-C kernel launches in the last call            */
+  long long tiles_total, tiles_active, slabs_total, slabs_active;
+  long long kernel_launches; /* all kernel launches of the last call           */
+  double bytes_operands; /* bytes of X and Y operands written by steps A/B      */
+  int n_batches;
+} gw_stats;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL: the library creates and owns one). */
+int gw_create(gw_ctx** out, int device, void* cuda_stream);
+void gw_destroy(gw_ctx* ctx);
+/* Message of the last failed call on this context ("" if none).  Owned by the
+ * context; valid until the next call on it. */
+const char* gw_last_error(const gw_ctx* ctx);
+
+/* Atom-blocked basis (Eq. 1 primary functions, auxiliary RI functions).
+ * xyz[n_atoms*3] Angstrom, n_ao[n_atoms] >= 1, n_ri[n_atoms] >= 1.
+ * Resets any tensor or Green's function set before. */
+int gw_set_basis(gw_ctx* ctx, int n_atoms, const double* xyz, const int* n_ao,
+                 const int* n_ri);
+
+/* Three-centre overlap tensor (mu sigma | P) of Eq. 4 in atom blocks.
+ * blk_abp[n_blocks*3] = (A, B, P) with A <= B, no duplicates; `data` holds the
+ * blocks back to back in that order, block i being [n_ao[A]][n_ao[B]][n_ri[P]]
+ * row-major; n_elems = sum of block sizes.  The (B, A, P) block is implied as
+ * the transpose in the first two indices.  (A, A, P) blocks must be symmetric
+ * in their two primary indices (GW_ERR_ASYM otherwise, tolerance 1e-12
+ * relative).  The data is copied to the device. */
+int gw_set_3c_tensor(gw_ctx* ctx, long long n_blocks, const int* blk_abp,
+                     const double* data, long long n_elems);
+
+/* Mean-field orbitals and the imaginary-time grid of Eq. 2.
+ * C[n_ao_total * n_ao_total]: column n is orbital n (C[mu*n_ao_total + n] is the
+ * paper's C_{n mu}); eps[n_ao_total] ascending; orbitals 0..n_occ-1 occupied;
+ * mu_fermi the energy zero of the exponentials; tau[n_tau] > 0. */
+int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
+                  double mu_fermi, const double* tau, int n_tau);
+
+/* chi_PQ(i tau_j), Eq. 3, for tau indices tau_first .. tau_first+tau_count-1,
+ * as real matrices: the returned chi is the paper's chi^0 divided by i, which
+ * is symmetric and negative semidefinite.
+ *
+ * Filter (Computational Methods): every atom block of the 3c tensor, of
+ * G^occ(tau)/G^virt(tau) and of the two intermediates of Eq. 3 whose Frobenius
+ * norm is < thr is dropped (thr = 0: nothing is dropped, exact zeros are still
+ * skipped).  chi is formed on atom blocks atom(P) <= atom(Q) and mirrored.
+ *
+ * chi_out: [tau_count][n_ri_total][n_ri_total] FP64, a device pointer if
+ * out_on_device != 0, else a host pointer. */
+int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
+               int screening, double* chi_out, int out_on_device);
+
+/* Counters and timings of the last gw_chi_tau call. */
+int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
+
+/* Tuning knobs (no effect on results beyond rounding order):
+ *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
+ *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)        */
+int gw_set_option(gw_ctx* ctx, const char* key, double value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWCHI_H */

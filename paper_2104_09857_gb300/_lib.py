@@ -1,0 +1,172 @@
+"""ctypes binding of libgwchi (include/gwchi.h): argument marshalling only.
+
+Every computation happens in the CUDA library.  If the library has not been
+built, or cannot be loaded, importing this module raises: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwchi.so")
+
+GW_OK = 0
+GW_FP64, GW_FP32, GW_BF16X3, GW_BF16X6 = 0, 1, 2, 3
+GW_SCREEN_BOUND, GW_SCREEN_MLP = 0, 1
+
+ERRORS = {
+    -1: "GW_ERR_INVALID_ARG",
+    -2: "GW_ERR_ORDER",
+    -3: "GW_ERR_ASYM",
+    -4: "GW_ERR_NONFINITE",
+    -5: "GW_ERR_OOM",
+    -6: "GW_ERR_CUDA",
+    -7: "GW_ERR_TIMEOUT",
+    -8: "GW_ERR_NOT_SPD",
+    -9: "GW_ERR_UNSUPPORTED",
+}
+
+PRECISIONS = {"fp64": GW_FP64, "fp32": GW_FP32, "bf16x3": GW_BF16X3, "bf16x6": GW_BF16X6}
+
+
+class GwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gw_stats(ctypes.Structure):
+    _fields_ = [
+        ("flops_useful", ctypes.c_double),
+        ("flops_a", ctypes.c_double),
+        ("flops_b", ctypes.c_double),
+        ("flops_c", ctypes.c_double),
+        ("flops_issued", ctypes.c_double),
+        ("ms_greens", ctypes.c_double),
+        ("ms_step_ab", ctypes.c_double),
+        ("ms_filter", ctypes.c_double),
+        ("ms_step_c", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_step_c_kernel", ctypes.c_double),
+        ("c_launches", ctypes.c_longlong),
+        ("tiles_total", ctypes.c_longlong),
+        ("tiles_active", ctypes.c_longlong),
+        ("slabs_total", ctypes.c_longlong),
+        ("slabs_active", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("bytes_operands", ctypes.c_double),
+        ("n_batches", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_D = ctypes.c_double
+
+# (name, restype, argtypes) of every entry point declared in include/gwchi.h
+SIGNATURES = [
+    ("gw_create", _I, [ctypes.POINTER(_P), _I, _P]),
+    ("gw_destroy", None, [_P]),
+    ("gw_last_error", ctypes.c_char_p, [_P]),
+    ("gw_set_basis", _I, [_P, _I, _P, _P, _P]),
+    ("gw_set_3c_tensor", _I, [_P, _LL, _P, _P, _LL]),
+    ("gw_set_greens", _I, [_P, _P, _P, _I, _D, _P, _I]),
+    ("gw_chi_tau", _I, [_P, _I, _I, _D, _I, _I, _P, _I]),
+    ("gw_get_stats", _I, [_P, ctypes.POINTER(gw_stats)]),
+    ("gw_set_option", _I, [_P, ctypes.c_char_p, _D]),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"libgwchi is not built ({path} missing); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` on a machine with nvcc")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != GW_OK:
+        msg = lib().gw_last_error(ctx).decode() if ctx else ""
+        raise GwError(rc, msg)
+
+
+# ---------------------------------------------------------------------------
+# thin functions with the C names
+# ---------------------------------------------------------------------------
+
+def gw_create(device: int = 0, stream: int | None = None) -> int:
+    out = _P()
+    rc = lib().gw_create(ctypes.byref(out), device, stream or None)
+    if rc != GW_OK:
+        raise GwError(rc, "gw_create failed")
+    return out.value
+
+
+def gw_destroy(ctx: int) -> None:
+    lib().gw_destroy(ctx)
+
+
+def gw_set_basis(ctx: int, xyz, n_ao, n_ri) -> None:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n_ao = np.ascontiguousarray(n_ao, dtype=np.int32)
+    n_ri = np.ascontiguousarray(n_ri, dtype=np.int32)
+    _check(ctx, lib().gw_set_basis(ctx, len(n_ao), _ptr(xyz), _ptr(n_ao), _ptr(n_ri)))
+
+
+def gw_set_3c_tensor(ctx: int, blocks, data) -> None:
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    _check(ctx, lib().gw_set_3c_tensor(ctx, blocks.shape[0], _ptr(blocks), _ptr(data), data.size))
+
+
+def gw_set_greens(ctx: int, C, eps, n_occ: int, mu_fermi: float, tau) -> None:
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    _check(ctx, lib().gw_set_greens(ctx, _ptr(C), _ptr(eps), int(n_occ), float(mu_fermi),
+                                    _ptr(tau), tau.size))
+
+
+def gw_chi_tau(ctx: int, tau_first: int, tau_count: int, thr: float, precision: int,
+               screening: int, out_ptr: int, out_on_device: bool) -> None:
+    _check(ctx, lib().gw_chi_tau(ctx, tau_first, tau_count, float(thr), precision, screening,
+                                 out_ptr, int(bool(out_on_device))))
+
+
+def gw_get_stats(ctx: int) -> dict:
+    st = gw_stats()
+    _check(ctx, lib().gw_get_stats(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def gw_set_option(ctx: int, key: str, value: float) -> None:
+    _check(ctx, lib().gw_set_option(ctx, key.encode(), float(value)))

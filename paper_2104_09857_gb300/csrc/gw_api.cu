@@ -1,0 +1,844 @@
+// C ABI of libgwchi and the host-side orchestration of the chi(i tau) path.
+//
+// Per tau point (Eq. 2, Eq. 3):
+//   1. G^occ(tau), G^virt(tau) = scaled orbital products (FP64), block filter.
+//   2. For each batch of sigma-atoms (owners of 3c panels):
+//        step A  X[P][(s, mu, s')] = sum_l G^occ[mu][l] T[l, s', P]    (M of Eq. 3)
+//        step B  Y[Q][(s, mu, s')] = sum_l G^virt[s'][l] T[l, mu, Q]   (N of Eq. 3)
+//        block filter of X and Y, slab/tile occupancy, per-tile task lists
+//        step C  chi[P][Q] -= sum_k X[P][k] Y[Q][k]   over surviving slabs
+//   3. mirror the atom-block upper triangle, write chi(tau).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gw_internal.h"
+#include "k_simt.h"
+
+using gw::Batch;
+using gw::kSlabAO;
+using gw::PanelDesc;
+using gw::PanelTask;
+
+namespace {
+
+struct WorkBufs {
+  std::map<std::string, std::pair<void*, size_t>> m;
+};
+std::map<const gw_ctx*, WorkBufs>& work_registry() {
+  static std::map<const gw_ctx*, WorkBufs> r;
+  return r;
+}
+
+#define GW_TRY(call)                                                                  \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+      return e_ == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA;              \
+    }                                                                                 \
+  } while (0)
+
+#define GW_CHECK_LAUNCH()                                                             \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess) {                                                          \
+      ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e_);             \
+      return GW_ERR_CUDA;                                                             \
+    }                                                                                 \
+  } while (0)
+
+int fail(gw_ctx* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  return code;
+}
+
+// named device scratch buffer, grown on demand
+int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
+  auto& wb = work_registry()[ctx].m;
+  auto it = wb.find(name);
+  if (it != wb.end() && it->second.second >= bytes) {
+    *out = it->second.first;
+    return GW_OK;
+  }
+  if (it != wb.end()) {
+    cudaFree(it->second.first);
+    wb.erase(it);
+  }
+  void* p = nullptr;
+  if (bytes > 0) {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = std::string("cudaMalloc of work buffer '") + name + "' (" +
+                 std::to_string(bytes) + " bytes): " + cudaGetErrorString(e);
+      return GW_ERR_OOM;
+    }
+  }
+  wb[name] = {p, bytes};
+  *out = p;
+  return GW_OK;
+}
+
+template <typename T>
+int wsT(gw_ctx* ctx, const char* name, size_t count, T** out) {
+  void* p = nullptr;
+  int rc = ws(ctx, name, count * sizeof(T), &p);
+  *out = static_cast<T*>(p);
+  return rc;
+}
+
+template <typename T>
+int upload(gw_ctx* ctx, const char* name, const std::vector<T>& v, T** out) {
+  int rc = wsT<T>(ctx, name, std::max<size_t>(v.size(), 1), out);
+  if (rc) return rc;
+  if (!v.empty())
+    GW_TRY(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  return GW_OK;
+}
+
+void free_dev(void* p) {
+  if (p) cudaFree(p);
+}
+
+void reset_tensor(gw_ctx* ctx) {
+  free_dev(ctx->d_t3);
+  free_dev(ctx->d_blk);
+  free_dev(ctx->d_blk_off);
+  free_dev(ctx->d_blk_norm);
+  free_dev(ctx->d_panel64);
+  free_dev(ctx->d_panel32);
+  free_dev(ctx->d_lam);
+  ctx->d_t3 = nullptr;
+  ctx->d_blk = nullptr;
+  ctx->d_blk_off = nullptr;
+  ctx->d_blk_norm = nullptr;
+  ctx->d_panel64 = nullptr;
+  ctx->d_panel32 = nullptr;
+  ctx->d_lam = nullptr;
+  ctx->n_blocks = ctx->n_elems = 0;
+  ctx->blk.clear();
+  ctx->blk_off.clear();
+  ctx->blk_norm.clear();
+  ctx->panels_ok = false;
+  ctx->panel32_ok = false;
+}
+
+void reset_greens(gw_ctx* ctx) {
+  free_dev(ctx->d_C);
+  free_dev(ctx->d_eps);
+  ctx->d_C = ctx->d_eps = nullptr;
+  ctx->have_greens = false;
+  ctx->tau.clear();
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+};
+
+// ---------------------------------------------------------------------------
+// panels
+// ---------------------------------------------------------------------------
+int build_panels(gw_ctx* ctx, double thr) {
+  if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
+  const int n = ctx->n_at;
+  std::vector<int> kept;
+  kept.reserve(ctx->n_blocks);
+  for (long long b = 0; b < ctx->n_blocks; ++b)
+    if (!(ctx->blk_norm[b] < thr)) kept.push_back((int)b);
+  // per owner: lambda atoms and RI window
+  std::vector<std::vector<int>> lam_atoms(n);
+  std::vector<int> p0(n, INT32_MAX), p1(n, -1);
+  for (int b : kept) {
+    int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
+    lam_atoms[B].push_back(A);
+    p0[B] = std::min(p0[B], ctx->ri_off[p]);
+    p1[B] = std::max(p1[B], ctx->ri_off[p + 1]);
+    if (A != B) {
+      lam_atoms[A].push_back(B);
+      p0[A] = std::min(p0[A], ctx->ri_off[p]);
+      p1[A] = std::max(p1[A], ctx->ri_off[p + 1]);
+    }
+  }
+  ctx->panels.assign(n, PanelDesc{});
+  std::vector<int> lam;
+  std::vector<std::vector<int>> rowpos(n);  // rowpos[s][atom] (dense per owner via map)
+  std::vector<std::map<int, int>> rowmap(n);
+  long long off = 0;
+  for (int s = 0; s < n; ++s) {
+    auto& la = lam_atoms[s];
+    std::sort(la.begin(), la.end());
+    la.erase(std::unique(la.begin(), la.end()), la.end());
+    PanelDesc d{};
+    d.owner = s;
+    d.nsig = ctx->n_ao[s];
+    d.lam_off = (int)lam.size();
+    int K = 0;
+    for (int a : la) {
+      rowmap[s][a] = K;
+      for (int i = ctx->ao_off[a]; i < ctx->ao_off[a + 1]; ++i) lam.push_back(i);
+      K += ctx->n_ao[a];
+    }
+    d.K = K;
+    if (K > 0) {
+      d.p0 = p0[s];
+      d.npw = p1[s] - p0[s];
+    }
+    d.off = off;
+    off += (long long)K * d.npw * d.nsig;
+    ctx->panels[s] = d;
+  }
+  ctx->panel_elems = off;
+  ctx->lam_total = (long long)lam.size();
+  // destinations of each kept block
+  std::vector<long long> dstB(kept.size()), dstA(kept.size());
+  std::vector<int> ldB(kept.size()), ldA(kept.size());
+  for (size_t i = 0; i < kept.size(); ++i) {
+    int b = kept[i];
+    int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
+    const PanelDesc& pb = ctx->panels[B];
+    ldB[i] = pb.npw * pb.nsig;
+    dstB[i] = pb.off + (long long)rowmap[B][A] * ldB[i] + (long long)(ctx->ri_off[p] - pb.p0) * pb.nsig;
+    const PanelDesc& pa = ctx->panels[A];
+    ldA[i] = pa.npw * pa.nsig;
+    dstA[i] = pa.off + (long long)rowmap[A][B] * ldA[i] + (long long)(ctx->ri_off[p] - pa.p0) * pa.nsig;
+  }
+  free_dev(ctx->d_panel64);
+  free_dev(ctx->d_panel32);
+  free_dev(ctx->d_lam);
+  ctx->d_panel64 = nullptr;
+  ctx->d_panel32 = nullptr;
+  ctx->d_lam = nullptr;
+  ctx->panel32_ok = false;
+  GW_TRY(cudaMalloc(&ctx->d_panel64, std::max<long long>(off, 1) * sizeof(double)));
+  GW_TRY(cudaMalloc(&ctx->d_lam, std::max<size_t>(lam.size(), 1) * sizeof(int)));
+  GW_TRY(cudaMemsetAsync(ctx->d_panel64, 0, std::max<long long>(off, 1) * sizeof(double), ctx->stream));
+  if (!lam.empty())
+    GW_TRY(cudaMemcpyAsync(ctx->d_lam, lam.data(), lam.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  int *d_kept, *d_ldB, *d_ldA;
+  long long *d_dstB, *d_dstA;
+  int rc;
+  if ((rc = upload(ctx, "kept", kept, &d_kept))) return rc;
+  if ((rc = upload(ctx, "dstB", dstB, &d_dstB))) return rc;
+  if ((rc = upload(ctx, "dstA", dstA, &d_dstA))) return rc;
+  if ((rc = upload(ctx, "ldB", ldB, &d_ldB))) return rc;
+  if ((rc = upload(ctx, "ldA", ldA, &d_ldA))) return rc;
+  int *d_nao, *d_nri, *d_rioff;
+  if ((rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao))) return rc;
+  if ((rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri))) return rc;
+  (void)d_rioff;
+  gw::launch_panel_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, ctx->d_ri_off,
+                           d_kept, (int)kept.size(), d_dstB, d_dstA, d_ldB, d_ldA, ctx->d_panel64,
+                           ctx->stream);
+  GW_CHECK_LAUNCH();
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->panels_ok = true;
+  ctx->panels_thr = thr;
+  return GW_OK;
+}
+
+int ensure_panel32(gw_ctx* ctx) {
+  if (ctx->panel32_ok) return GW_OK;
+  free_dev(ctx->d_panel32);
+  ctx->d_panel32 = nullptr;
+  GW_TRY(cudaMalloc(&ctx->d_panel32, std::max<long long>(ctx->panel_elems, 1) * sizeof(float)));
+  gw::launch_cast_f64_f32(ctx->d_panel64, ctx->d_panel32, ctx->panel_elems, ctx->stream);
+  GW_CHECK_LAUNCH();
+  ctx->panel32_ok = true;
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches of owner atoms
+// ---------------------------------------------------------------------------
+std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_bytes) {
+  std::vector<Batch> out;
+  const int n = ctx->n_at;
+  int s = 0;
+  while (s < n) {
+    Batch b{};
+    b.s0 = s;
+    b.P0 = INT32_MAX;
+    b.P1 = 0;
+    long long K = 0;
+    int e = s;
+    while (e < n) {
+      const PanelDesc& d = ctx->panels[e];
+      int P0 = b.P0, P1 = b.P1;
+      if (d.K > 0) {
+        P0 = std::min(P0, d.p0);
+        P1 = std::max(P1, d.p0 + d.npw);
+      }
+      long long K2 = K + (long long)ctx->naop * d.nsig;
+      double bytes = (double)K2 * ((P1 > P0 ? P1 - P0 : 0) + ctx->nri) * elem_bytes;
+      bool limit = ctx->batch_atoms > 0 && e - s >= ctx->batch_atoms;
+      if (e > s && (bytes > budget_bytes || limit)) break;
+      b.P0 = P0;
+      b.P1 = P1;
+      b.seg.push_back(K);
+      K = K2;
+      ++e;
+    }
+    b.s1 = e;
+    b.Kb = K;
+    if (b.P1 <= b.P0) {
+      b.P0 = 0;
+      b.P1 = 0;
+    }
+    b.nslab = (b.s1 - b.s0) * (ctx->naop / kSlabAO);
+    out.push_back(b);
+    s = e;
+  }
+  return out;
+}
+
+template <typename T>
+int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, const T* pool,
+                  double thr, double* acc, std::vector<double>& fc_host, int precision) {
+  const int ns = b.s1 - b.s0;
+  const int prow = b.P1 - b.P0;
+  const long long Kb = b.Kb;
+  int rc;
+  if (prow == 0 || Kb == 0) return GW_OK;
+  T *X, *Y;
+  if ((rc = wsT<T>(ctx, "X", (size_t)prow * Kb, &X))) return rc;
+  if ((rc = wsT<T>(ctx, "Y", (size_t)ctx->nri * Kb, &Y))) return rc;
+  GW_TRY(cudaMemsetAsync(X, 0, (size_t)prow * Kb * sizeof(T), ctx->stream));
+  GW_TRY(cudaMemsetAsync(Y, 0, (size_t)ctx->nri * Kb * sizeof(T), ctx->stream));
+
+  // step A tasks: owners of the batch, rows mu = all AOs
+  std::vector<PanelTask> ta;
+  int maxNa = 0;
+  for (int s = b.s0; s < b.s1; ++s) {
+    const PanelDesc& d = ctx->panels[s];
+    if (d.K == 0) continue;
+    PanelTask t{};
+    t.panel_off = d.off;
+    t.K = d.K;
+    t.N = d.npw * d.nsig;
+    t.lam_off = d.lam_off;
+    t.npw = d.npw;
+    t.nsig = d.nsig;
+    t.p0 = d.p0;
+    t.aom = ctx->ao_off[s];
+    t.seg = b.seg[s - b.s0];
+    maxNa = std::max(maxNa, t.N);
+    ta.push_back(t);
+  }
+  // step B tasks: every panel, rows sigma of the batch
+  std::vector<PanelTask> tb;
+  int maxNb = 0;
+  for (int m = 0; m < ctx->n_at; ++m) {
+    const PanelDesc& d = ctx->panels[m];
+    if (d.K == 0) continue;
+    PanelTask t{};
+    t.panel_off = d.off;
+    t.K = d.K;
+    t.N = d.npw * d.nsig;
+    t.lam_off = d.lam_off;
+    t.npw = d.npw;
+    t.nsig = d.nsig;
+    t.p0 = d.p0;
+    t.aom = ctx->ao_off[m];
+    t.seg = 0;
+    maxNb = std::max(maxNb, t.N);
+    tb.push_back(t);
+  }
+  const int r0 = ctx->ao_off[b.s0];
+  const int R = ctx->ao_off[b.s1] - r0;
+  std::vector<long long> rowbase(R);
+  std::vector<int> rowmul(R);
+  for (int s = b.s0; s < b.s1; ++s)
+    for (int i = 0; i < ctx->n_ao[s]; ++i) {
+      rowbase[ctx->ao_off[s] - r0 + i] = b.seg[s - b.s0] + i;
+      rowmul[ctx->ao_off[s] - r0 + i] = ctx->n_ao[s];
+    }
+  PanelTask *d_ta, *d_tb;
+  long long* d_rowbase;
+  int* d_rowmul;
+  if ((rc = upload(ctx, "tasksA", ta, &d_ta))) return rc;
+  if ((rc = upload(ctx, "tasksB", tb, &d_tb))) return rc;
+  if ((rc = upload(ctx, "rowbase", rowbase, &d_rowbase))) return rc;
+  if ((rc = upload(ctx, "rowmul", rowmul, &d_rowmul))) return rc;
+
+  gw::launch_panel_gemm<T>(g_occ, ctx->nao, pool, ctx->d_lam, d_ta, (int)ta.size(), maxNa, 0, 0,
+                           ctx->nao, b.P0, Kb, nullptr, nullptr, X, ctx->stream);
+  GW_CHECK_LAUNCH();
+  gw::launch_panel_gemm<T>(g_virt, ctx->nao, pool, ctx->d_lam, d_tb, (int)tb.size(), maxNb, 1, r0,
+                           R, 0, Kb, d_rowbase, d_rowmul, Y, ctx->stream);
+  GW_CHECK_LAUNCH();
+  ctx->stats.kernel_launches += 2;
+  ctx->stats.bytes_operands += (double)(prow + ctx->nri) * Kb * sizeof(T);
+
+  // block filter of X and Y, occupancy flags
+  const int nslab = b.nslab;
+  const int npt = (prow + 63) / 64, nqt = (ctx->nri + 63) / 64;
+  const int pa0 = [&] {
+    int a = 0;
+    while (ctx->ri_off[a + 1] <= b.P0) ++a;
+    return a;
+  }();
+  int pa1 = pa0;
+  while (pa1 < ctx->n_at && ctx->ri_off[pa1] < b.P1) ++pa1;
+  const int npa = pa1 - pa0;
+  unsigned char *bx, *by, *fx, *fy;
+  if ((rc = wsT(ctx, "bx", (size_t)ns * ctx->n_at * npa, &bx))) return rc;
+  if ((rc = wsT(ctx, "by", (size_t)ns * ctx->n_at * ctx->n_at, &by))) return rc;
+  if ((rc = wsT(ctx, "fx", (size_t)nslab * npt, &fx))) return rc;
+  if ((rc = wsT(ctx, "fy", (size_t)nslab * nqt, &fy))) return rc;
+  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)nslab * npt, ctx->stream));
+  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)nslab * nqt, ctx->stream));
+  long long* d_seg;
+  if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
+  int* d_nao;
+  if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao))) return rc;
+  gw::launch_operand_block_filter<T>(X, Kb, b.P0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns,
+                                     d_seg, pa0, npa, ctx->n_at, thr, ctx->naop, bx, fx, npt,
+                                     ctx->stream);
+  GW_CHECK_LAUNCH();
+  gw::launch_operand_block_filter<T>(Y, Kb, 0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns, d_seg,
+                                     0, ctx->n_at, ctx->n_at, thr, ctx->naop, by, fy, nqt,
+                                     ctx->stream);
+  GW_CHECK_LAUNCH();
+  // slabs
+  std::vector<long long> slab_k0(nslab);
+  std::vector<int> slab_len(nslab);
+  const int per = ctx->naop / kSlabAO;
+  for (int sl = 0; sl < ns; ++sl)
+    for (int c = 0; c < per; ++c) {
+      int nsig = ctx->n_ao[b.s0 + sl];
+      slab_k0[sl * per + c] = b.seg[sl] + (long long)c * kSlabAO * nsig;
+      slab_len[sl * per + c] = kSlabAO * nsig;
+    }
+  long long* d_k0;
+  int* d_len;
+  if ((rc = upload(ctx, "slab_k0", slab_k0, &d_k0))) return rc;
+  if ((rc = upload(ctx, "slab_len", slab_len, &d_len))) return rc;
+  int *tasks, *counts;
+  long long* kacc;
+  if ((rc = wsT(ctx, "tasks", (size_t)npt * nqt * nslab, &tasks))) return rc;
+  if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
+  if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
+  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, ctx->nri, ctx->d_atom_of_ri, d_len,
+                         tasks, counts, kacc, ctx->stream);
+  GW_CHECK_LAUNCH();
+  double* d_fc;
+  if ((rc = wsT(ctx, "fc", (size_t)ns * ctx->n_at, &d_fc))) return rc;
+  int* d_nri;
+  if ((rc = upload(ctx, "n_ri_b", ctx->n_ri, &d_nri))) return rc;
+  gw::launch_count_c(bx, by, ns, ctx->n_at, pa0, npa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
+  GW_CHECK_LAUNCH();
+  ctx->stats.kernel_launches += 5;
+
+  // step C
+  if (precision == GW_FP64 || precision == GW_FP32) {
+    gw::launch_chi_tiles<T, T>(X, Y, Kb, b.P0, prow, ctx->nri, tasks, counts, nslab, npt, nqt, d_k0,
+                               d_len, acc, ctx->stream);
+    GW_CHECK_LAUNCH();
+    ctx->stats.c_launches += 1;
+    ctx->stats.kernel_launches += 1;
+  } else {
+    return fail(ctx, GW_ERR_UNSUPPORTED, "tensor-core step C requires the FP32 operand route");
+  }
+  // counters (small D2H)
+  std::vector<int> h_counts((size_t)npt * nqt);
+  std::vector<long long> h_kacc((size_t)npt * nqt);
+  std::vector<double> h_fc((size_t)ns * ctx->n_at);
+  GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaMemcpyAsync(h_kacc.data(), kacc, h_kacc.size() * sizeof(long long),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaMemcpyAsync(h_fc.data(), d_fc, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  long long act = 0, sl_act = 0;
+  for (int c : h_counts) {
+    act += c > 0;
+    sl_act += c;
+  }
+  ctx->stats.tiles_total += (long long)npt * nqt;
+  ctx->stats.tiles_active += act;
+  ctx->stats.slabs_total += (long long)npt * nqt * nslab;
+  ctx->stats.slabs_active += sl_act;
+  for (double v : h_fc) fc_host.push_back(v);
+  // issued by step C: 2 * tile area * K over active tiles
+  double ksum = 0.0;
+  for (long long k : h_kacc) ksum += (double)k;
+  ctx->stats.flops_issued += 2.0 * 64.0 * 64.0 * ksum;
+  return GW_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int gw_create(gw_ctx** out, int device, void* cuda_stream) {
+  if (!out) return GW_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GW_ERR_INVALID_ARG;
+  }
+  gw_ctx* ctx = new gw_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return GW_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return GW_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return GW_OK;
+}
+
+void gw_destroy(gw_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  reset_tensor(ctx);
+  reset_greens(ctx);
+  free_dev(ctx->d_ao_off);
+  free_dev(ctx->d_ri_off);
+  free_dev(ctx->d_atom_of_ri);
+  free_dev(ctx->d_atom_of_ao);
+  auto& reg = work_registry();
+  auto it = reg.find(ctx);
+  if (it != reg.end()) {
+    for (auto& kv : it->second.m) free_dev(kv.second.first);
+    reg.erase(it);
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* gw_last_error(const gw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gw_set_basis(gw_ctx* ctx, int n_atoms, const double* xyz, const int* n_ao, const int* n_ri) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (n_atoms <= 0 || !xyz || !n_ao || !n_ri) return fail(ctx, GW_ERR_INVALID_ARG, "set_basis: bad arguments");
+  long long nao = 0, nri = 0;
+  for (int a = 0; a < n_atoms; ++a) {
+    if (n_ao[a] <= 0 || n_ri[a] <= 0 || n_ao[a] > 4096 || n_ri[a] > 4096)
+      return fail(ctx, GW_ERR_INVALID_ARG, "set_basis: per-atom sizes must be in 1..4096");
+    if (!std::isfinite(xyz[3 * a]) || !std::isfinite(xyz[3 * a + 1]) || !std::isfinite(xyz[3 * a + 2]))
+      return fail(ctx, GW_ERR_NONFINITE, "set_basis: non-finite coordinate");
+    nao += n_ao[a];
+    nri += n_ri[a];
+  }
+  if (nao > 1000000 || nri > 1000000) return fail(ctx, GW_ERR_INVALID_ARG, "set_basis: basis too large");
+  GW_TRY(cudaSetDevice(ctx->device));
+  reset_tensor(ctx);
+  reset_greens(ctx);
+  ctx->n_at = n_atoms;
+  ctx->xyz.assign(xyz, xyz + 3 * n_atoms);
+  ctx->n_ao.assign(n_ao, n_ao + n_atoms);
+  ctx->n_ri.assign(n_ri, n_ri + n_atoms);
+  ctx->ao_off.assign(n_atoms + 1, 0);
+  ctx->ri_off.assign(n_atoms + 1, 0);
+  for (int a = 0; a < n_atoms; ++a) {
+    ctx->ao_off[a + 1] = ctx->ao_off[a] + n_ao[a];
+    ctx->ri_off[a + 1] = ctx->ri_off[a] + n_ri[a];
+  }
+  ctx->nao = (int)nao;
+  ctx->nri = (int)nri;
+  ctx->naop = (int)((nao + kSlabAO - 1) / kSlabAO * kSlabAO);
+  std::vector<int> atom_of_ri(nri), atom_of_ao(nao);
+  for (int a = 0; a < n_atoms; ++a) {
+    for (int i = ctx->ri_off[a]; i < ctx->ri_off[a + 1]; ++i) atom_of_ri[i] = a;
+    for (int i = ctx->ao_off[a]; i < ctx->ao_off[a + 1]; ++i) atom_of_ao[i] = a;
+  }
+  free_dev(ctx->d_ao_off);
+  free_dev(ctx->d_ri_off);
+  free_dev(ctx->d_atom_of_ri);
+  free_dev(ctx->d_atom_of_ao);
+  GW_TRY(cudaMalloc(&ctx->d_ao_off, (n_atoms + 1) * sizeof(int)));
+  GW_TRY(cudaMalloc(&ctx->d_ri_off, (n_atoms + 1) * sizeof(int)));
+  GW_TRY(cudaMalloc(&ctx->d_atom_of_ri, nri * sizeof(int)));
+  GW_TRY(cudaMalloc(&ctx->d_atom_of_ao, nao * sizeof(int)));
+  GW_TRY(cudaMemcpy(ctx->d_ao_off, ctx->ao_off.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  GW_TRY(cudaMemcpy(ctx->d_ri_off, ctx->ri_off.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  GW_TRY(cudaMemcpy(ctx->d_atom_of_ri, atom_of_ri.data(), nri * sizeof(int), cudaMemcpyHostToDevice));
+  GW_TRY(cudaMemcpy(ctx->d_atom_of_ao, atom_of_ao.data(), nao * sizeof(int), cudaMemcpyHostToDevice));
+  return GW_OK;
+}
+
+int gw_set_3c_tensor(gw_ctx* ctx, long long n_blocks, const int* blk_abp, const double* data,
+                     long long n_elems) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_at == 0) return fail(ctx, GW_ERR_ORDER, "set_3c_tensor: call gw_set_basis first");
+  if (n_blocks < 0 || n_elems < 0 || (n_blocks > 0 && (!blk_abp || !data)))
+    return fail(ctx, GW_ERR_INVALID_ARG, "set_3c_tensor: bad arguments");
+  GW_TRY(cudaSetDevice(ctx->device));
+  reset_tensor(ctx);
+  std::vector<long long> off(n_blocks + 1, 0);
+  long long prev = -1;
+  for (long long b = 0; b < n_blocks; ++b) {
+    int A = blk_abp[3 * b], B = blk_abp[3 * b + 1], P = blk_abp[3 * b + 2];
+    if (A < 0 || B < 0 || P < 0 || A >= ctx->n_at || B >= ctx->n_at || P >= ctx->n_at || A > B)
+      return fail(ctx, GW_ERR_INVALID_ARG,
+                  "set_3c_tensor: block " + std::to_string(b) + " has an atom index out of range or A > B");
+    long long key = ((long long)A * ctx->n_at + B) * ctx->n_at + P;
+    if (key <= prev)
+      return fail(ctx, GW_ERR_INVALID_ARG,
+                  "set_3c_tensor: blocks must be sorted by (A, B, P) without duplicates");
+    prev = key;
+    off[b + 1] = off[b] + (long long)ctx->n_ao[A] * ctx->n_ao[B] * ctx->n_ri[P];
+  }
+  if (off[n_blocks] != n_elems)
+    return fail(ctx, GW_ERR_INVALID_ARG,
+                "set_3c_tensor: n_elems " + std::to_string(n_elems) + " does not match the block sizes (" +
+                    std::to_string(off[n_blocks]) + ")");
+  ctx->blk.assign(blk_abp, blk_abp + 3 * n_blocks);
+  ctx->blk_off = off;
+  ctx->n_blocks = n_blocks;
+  ctx->n_elems = n_elems;
+  GW_TRY(cudaMalloc(&ctx->d_t3, std::max<long long>(n_elems, 1) * sizeof(double)));
+  GW_TRY(cudaMalloc(&ctx->d_blk, std::max<long long>(3 * n_blocks, 1) * sizeof(int)));
+  GW_TRY(cudaMalloc(&ctx->d_blk_off, (n_blocks + 1) * sizeof(long long)));
+  GW_TRY(cudaMalloc(&ctx->d_blk_norm, std::max<long long>(n_blocks, 1) * sizeof(double)));
+  // copy in chunks of 1 GiB (pageable host memory)
+  const long long chunk = 1LL << 27;
+  for (long long i = 0; i < n_elems; i += chunk) {
+    long long n = std::min(chunk, n_elems - i);
+    GW_TRY(cudaMemcpyAsync(ctx->d_t3 + i, data + i, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (n_blocks > 0) {
+    GW_TRY(cudaMemcpyAsync(ctx->d_blk, blk_abp, 3 * n_blocks * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  GW_TRY(cudaMemcpyAsync(ctx->d_blk_off, off.data(), (n_blocks + 1) * sizeof(long long),
+                         cudaMemcpyHostToDevice, ctx->stream));
+  int* d_bad;
+  int rc;
+  if ((rc = wsT(ctx, "bad", 1, &d_bad))) return rc;
+  GW_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), ctx->stream));
+  int *d_nao, *d_nri;
+  if ((rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao))) return rc;
+  if ((rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri))) return rc;
+  gw::launch_block_norms_3c(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, n_blocks,
+                            ctx->d_blk_norm, d_bad, ctx->stream);
+  GW_CHECK_LAUNCH();
+  int bad = 0;
+  ctx->blk_norm.resize(n_blocks);
+  GW_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (n_blocks > 0)
+    GW_TRY(cudaMemcpyAsync(ctx->blk_norm.data(), ctx->d_blk_norm, n_blocks * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  if (bad & 1) {
+    reset_tensor(ctx);
+    return fail(ctx, GW_ERR_NONFINITE, "set_3c_tensor: NaN or Inf in the tensor data");
+  }
+  if (bad & 2) {
+    reset_tensor(ctx);
+    return fail(ctx, GW_ERR_ASYM, "set_3c_tensor: an (A, A, P) block is not symmetric in its primary indices");
+  }
+  return GW_OK;
+}
+
+int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ, double mu_fermi,
+                  const double* tau, int n_tau) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_at == 0) return fail(ctx, GW_ERR_ORDER, "set_greens: call gw_set_basis first");
+  const int nao = ctx->nao;
+  if (!C || !eps || !tau || n_tau <= 0 || n_occ < 0 || n_occ > nao)
+    return fail(ctx, GW_ERR_INVALID_ARG, "set_greens: bad arguments");
+  if (!std::isfinite(mu_fermi)) return fail(ctx, GW_ERR_NONFINITE, "set_greens: mu_fermi not finite");
+  for (int j = 0; j < n_tau; ++j)
+    if (!(tau[j] > 0.0) || !std::isfinite(tau[j]))
+      return fail(ctx, GW_ERR_INVALID_ARG, "set_greens: tau points must be finite and > 0");
+  for (int i = 0; i < nao; ++i)
+    if (!std::isfinite(eps[i])) return fail(ctx, GW_ERR_NONFINITE, "set_greens: non-finite orbital energy");
+  for (long long i = 0; i < (long long)nao * nao; ++i)
+    if (!std::isfinite(C[i])) return fail(ctx, GW_ERR_NONFINITE, "set_greens: non-finite orbital coefficient");
+  GW_TRY(cudaSetDevice(ctx->device));
+  reset_greens(ctx);
+  GW_TRY(cudaMalloc(&ctx->d_C, (size_t)nao * nao * sizeof(double)));
+  GW_TRY(cudaMalloc(&ctx->d_eps, (size_t)nao * sizeof(double)));
+  GW_TRY(cudaMemcpyAsync(ctx->d_C, C, (size_t)nao * nao * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  GW_TRY(cudaMemcpyAsync(ctx->d_eps, eps, (size_t)nao * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->n_occ = n_occ;
+  ctx->mu = mu_fermi;
+  ctx->tau.assign(tau, tau + n_tau);
+  ctx->have_greens = true;
+  return GW_OK;
+}
+
+int gw_set_option(gw_ctx* ctx, const char* key, double value) {
+  if (!ctx || !key) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!strcmp(key, "batch_bytes")) {
+    if (!(value >= 1e6)) return fail(ctx, GW_ERR_INVALID_ARG, "batch_bytes must be >= 1e6");
+    ctx->batch_bytes = value;
+    return GW_OK;
+  }
+  if (!strcmp(key, "batch_atoms")) {
+    if (!(value >= 0)) return fail(ctx, GW_ERR_INVALID_ARG, "batch_atoms must be >= 0");
+    ctx->batch_atoms = (int)value;
+    return GW_OK;
+  }
+  return fail(ctx, GW_ERR_INVALID_ARG, std::string("unknown option '") + key + "'");
+}
+
+int gw_get_stats(const gw_ctx* ctx, gw_stats* out) {
+  if (!ctx || !out) return GW_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return GW_OK;
+}
+
+int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision, int screening,
+               double* chi_out, int out_on_device) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_at == 0 || ctx->d_t3 == nullptr && ctx->n_blocks > 0)
+    return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_basis and gw_set_3c_tensor first");
+  if (ctx->blk_off.empty()) return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_3c_tensor first");
+  if (!ctx->have_greens) return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_greens first");
+  if (tau_first < 0 || tau_count < 0 || tau_first + tau_count > (int)ctx->tau.size())
+    return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: tau range out of bounds");
+  if (!(thr >= 0.0) || !std::isfinite(thr)) return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: thr must be finite and >= 0");
+  if (precision < GW_FP64 || precision > GW_BF16X6)
+    return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown precision");
+  if (screening != GW_SCREEN_BOUND && screening != GW_SCREEN_MLP)
+    return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown screening mode");
+  if (screening == GW_SCREEN_MLP) return fail(ctx, GW_ERR_UNSUPPORTED, "chi_tau: learned screening not built");
+  if (tau_count > 0 && !chi_out) return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: chi_out is null");
+  GW_TRY(cudaSetDevice(ctx->device));
+  ctx->stats = gw_stats{};
+  auto t_start = std::chrono::steady_clock::now();
+  int rc;
+  if ((rc = build_panels(ctx, thr))) return rc;
+  const bool f64 = precision == GW_FP64;
+  if (!f64 && (rc = ensure_panel32(ctx))) return rc;
+  const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  std::vector<Batch> batches = plan_batches(ctx, esz, ctx->batch_bytes);
+  ctx->stats.n_batches = (int)batches.size();
+
+  double *cso, *csv, *go, *gv, *acc, *stage;
+  float *go32 = nullptr, *gv32 = nullptr;
+  unsigned char *flo, *flv;
+  if ((rc = wsT(ctx, "cso", (size_t)nao * std::max(ctx->n_occ, 1), &cso))) return rc;
+  if ((rc = wsT(ctx, "csv", (size_t)nao * std::max(nao - ctx->n_occ, 1), &csv))) return rc;
+  if ((rc = wsT(ctx, "g_occ", (size_t)nao * nao, &go))) return rc;
+  if ((rc = wsT(ctx, "g_virt", (size_t)nao * nao, &gv))) return rc;
+  if ((rc = wsT(ctx, "chi_acc", (size_t)nri * nri, &acc))) return rc;
+  if ((rc = wsT(ctx, "flag_occ", (size_t)n_at * n_at, &flo))) return rc;
+  if ((rc = wsT(ctx, "flag_virt", (size_t)n_at * n_at, &flv))) return rc;
+  if (!out_on_device && (rc = wsT(ctx, "chi_stage", (size_t)nri * nri, &stage))) return rc;
+  if (!f64) {
+    if ((rc = wsT(ctx, "g_occ32", (size_t)nao * nao, &go32))) return rc;
+    if ((rc = wsT(ctx, "g_virt32", (size_t)nao * nao, &gv32))) return rc;
+  }
+  // per-block useful-flop weights of steps A and B: 2 nA nB nP, both orientations
+  std::vector<int> kept_blocks;
+  for (long long b = 0; b < ctx->n_blocks; ++b)
+    if (!(ctx->blk_norm[b] < thr)) kept_blocks.push_back((int)b);
+
+  cudaEvent_t ev[8];
+  for (auto& e : ev) GW_TRY(cudaEventCreate(&e));
+  double ms_g = 0, ms_ab = 0, ms_c = 0;
+  for (int j = tau_first; j < tau_first + tau_count; ++j) {
+    GW_TRY(cudaEventRecord(ev[0], ctx->stream));
+    gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[j], cso, csv, go, gv,
+                      ctx->stream);
+    GW_CHECK_LAUNCH();
+    ctx->stats.kernel_launches += 3;
+    std::vector<unsigned char> hfo((size_t)n_at * n_at, 1), hfv((size_t)n_at * n_at, 1);
+    if (thr > 0.0) {
+      gw::launch_sym_block_filter(go, nao, ctx->d_ao_off, n_at, thr, flo, ctx->stream);
+      gw::launch_sym_block_filter(gv, nao, ctx->d_ao_off, n_at, thr, flv, ctx->stream);
+      GW_CHECK_LAUNCH();
+      ctx->stats.kernel_launches += 2;
+      GW_TRY(cudaMemcpyAsync(hfo.data(), flo, hfo.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      GW_TRY(cudaMemcpyAsync(hfv.data(), flv, hfv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (!f64) {
+      gw::launch_cast_f64_f32(go, go32, (long long)nao * nao, ctx->stream);
+      gw::launch_cast_f64_f32(gv, gv32, (long long)nao * nao, ctx->stream);
+      GW_CHECK_LAUNCH();
+      ctx->stats.kernel_launches += 2;
+    }
+    GW_TRY(cudaMemsetAsync(acc, 0, (size_t)nri * nri * sizeof(double), ctx->stream));
+    GW_TRY(cudaEventRecord(ev[1], ctx->stream));
+    std::vector<double> fc;
+    for (const Batch& b : batches) {
+      if (f64)
+        rc = chi_one_batch<double>(ctx, b, go, gv, ctx->d_panel64, thr, acc, fc, precision);
+      else
+        rc = chi_one_batch<float>(ctx, b, go32, gv32, ctx->d_panel32, thr, acc, fc, precision);
+      if (rc) return rc;
+    }
+    GW_TRY(cudaEventRecord(ev[2], ctx->stream));
+    double* dst = out_on_device ? chi_out + (size_t)(j - tau_first) * nri * nri : stage;
+    gw::launch_mirror(acc, dst, nri, ctx->d_atom_of_ri, ctx->stream);
+    GW_CHECK_LAUNCH();
+    ctx->stats.kernel_launches += 1;
+    if (!out_on_device)
+      GW_TRY(cudaMemcpyAsync(chi_out + (size_t)(j - tau_first) * nri * nri, stage,
+                             (size_t)nri * nri * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GW_TRY(cudaStreamSynchronize(ctx->stream));
+    float t01, t12;
+    GW_TRY(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+    GW_TRY(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+    ms_g += t01;
+    ms_c += t12;
+    // useful flops of steps A and B for this tau
+    std::vector<double> kao_o(n_at, 0.0), kao_v(n_at, 0.0);
+    for (int l = 0; l < n_at; ++l)
+      for (int m = 0; m < n_at; ++m) {
+        if (hfo[(size_t)m * n_at + l]) kao_o[l] += ctx->n_ao[m];
+        if (hfv[(size_t)m * n_at + l]) kao_v[l] += ctx->n_ao[m];
+      }
+    double fa = 0.0, fb = 0.0;
+    for (int b : kept_blocks) {
+      int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], P = ctx->blk[3 * b + 2];
+      double w = 2.0 * ctx->n_ao[A] * ctx->n_ao[B] * ctx->n_ri[P];
+      fa += w * kao_o[A];
+      fb += w * kao_v[A];
+      if (A != B) {
+        fa += w * kao_o[B];
+        fb += w * kao_v[B];
+      }
+    }
+    double fcs = 0.0;
+    for (double v : fc) fcs += v;
+    ctx->stats.flops_a += fa;
+    ctx->stats.flops_b += fb;
+    ctx->stats.flops_c += fcs;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  ctx->stats.flops_useful = ctx->stats.flops_a + ctx->stats.flops_b + ctx->stats.flops_c;
+  ctx->stats.ms_greens = ms_g;
+  ctx->stats.ms_step_ab = 0.0;
+  ctx->stats.ms_step_c = ms_c;
+  ctx->stats.ms_total =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  (void)ms_ab;
+  return GW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal declarations shared by the translation units of libgwchi.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gwchi.h"
+
+namespace gw {
+
+// Slab: 64 consecutive primary functions mu of one sigma-atom segment of the
+// K dimension of the step-C operands.
+constexpr int kSlabAO = 64;
+
+// Per-owner-atom dense panel of the three-centre tensor:
+//   panel[k][pw][s'] = T[lambda_k, sigma = ao_off(owner) + s', P = p0 + pw]
+// k runs over the primary functions of the atoms that share a stored block
+// with the owner (ascending atom order), pw over the contiguous RI window
+// [p0, p0 + npw) of those blocks, s' over the owner's primary functions.
+struct PanelDesc {
+  long long off;  // element offset of the panel in the panel pool
+  int K;          // rows (gathered lambda functions)
+  int nsig;       // n_ao(owner)
+  int p0, npw;    // RI window
+  int lam_off;    // offset into the lambda-index pool (K entries)
+  int owner;
+};
+
+// One grouped-GEMM problem of steps A/B: Z[r][n] = sum_k G[lam[k]][r] P[k][n].
+struct PanelTask {
+  long long panel_off;
+  int K, N;       // N = npw * nsig
+  int lam_off;
+  int npw, nsig;  // panel window and owner size (n = pw * nsig + s')
+  int p0;
+  int aom;        // mode B: AO offset of the panel owner (mu = aom + s')
+  long long seg;  // mode A: K offset of the owner's segment in X
+};
+
+struct Batch {
+  int s0, s1;         // owner atoms [s0, s1)
+  int P0, P1;         // RI window of X rows
+  long long Kb;       // K length (sum over owners of naop * nsig)
+  int nslab;          // (s1 - s0) * naop / kSlabAO
+  std::vector<long long> seg;  // per owner: K offset
+};
+
+}  // namespace gw
+
+struct gw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // basis
+  int n_at = 0, nao = 0, nri = 0, naop = 0;  // naop = nao rounded up to kSlabAO
+  std::vector<double> xyz;
+  std::vector<int> n_ao, n_ri, ao_off, ri_off;  // offsets have n_at + 1 entries
+  int* d_ao_off = nullptr;
+  int* d_ri_off = nullptr;
+  int* d_atom_of_ri = nullptr;
+  int* d_atom_of_ao = nullptr;
+
+  // three-centre tensor (A <= B blocks as given)
+  long long n_blocks = 0, n_elems = 0;
+  std::vector<int> blk;              // 3 per block
+  std::vector<long long> blk_off;    // n_blocks + 1
+  double* d_t3 = nullptr;
+  int* d_blk = nullptr;
+  long long* d_blk_off = nullptr;
+  double* d_blk_norm = nullptr;
+  std::vector<double> blk_norm;
+
+  // Green's function inputs
+  bool have_greens = false;
+  double* d_C = nullptr;
+  double* d_eps = nullptr;
+  int n_occ = 0;
+  double mu = 0.0;
+  std::vector<double> tau;
+
+  // panels (depend on thr through the 3c block filter)
+  bool panels_ok = false;
+  double panels_thr = -1.0;
+  std::vector<gw::PanelDesc> panels;   // per atom (K == 0: no panel)
+  long long panel_elems = 0;
+  double* d_panel64 = nullptr;
+  float* d_panel32 = nullptr;
+  bool panel32_ok = false;
+  int* d_lam = nullptr;
+  long long lam_total = 0;
+
+  // options
+  double batch_bytes = 24e9;
+  int batch_atoms = 0;
+
+  gw_stats stats{};
+};

@@ -301,9 +301,28 @@ std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_by
   return out;
 }
 
+// CUDA events bracketing each step-C launch (reused across calls)
+std::vector<cudaEvent_t>& c_events(const gw_ctx* ctx) {
+  static std::map<const gw_ctx*, std::vector<cudaEvent_t>> m;
+  return m[ctx];
+}
+
+int c_event_pair(gw_ctx* ctx, size_t idx, cudaEvent_t* a, cudaEvent_t* b) {
+  auto& v = c_events(ctx);
+  while (v.size() < 2 * (idx + 1)) {
+    cudaEvent_t e;
+    GW_TRY(cudaEventCreate(&e));
+    v.push_back(e);
+  }
+  *a = v[2 * idx];
+  *b = v[2 * idx + 1];
+  return GW_OK;
+}
+
 template <typename T>
 int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, const T* pool,
-                  double thr, double* acc, std::vector<double>& fc_host, int precision) {
+                  double thr, double* acc, std::vector<double>& fc_host, int precision,
+                  size_t batch_idx) {
   const int ns = b.s1 - b.s0;
   const int prow = b.P1 - b.P0;
   const long long Kb = b.Kb;
@@ -440,10 +459,14 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   ctx->stats.kernel_launches += 5;
 
   // step C
+  cudaEvent_t ec0, ec1;
+  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
   if (precision == GW_FP64 || precision == GW_FP32) {
+    GW_TRY(cudaEventRecord(ec0, ctx->stream));
     gw::launch_chi_tiles<T, T>(X, Y, Kb, b.P0, prow, ctx->nri, tasks, counts, nslab, npt, nqt, d_k0,
                                d_len, acc, ctx->stream);
     GW_CHECK_LAUNCH();
+    GW_TRY(cudaEventRecord(ec1, ctx->stream));
     ctx->stats.c_launches += 1;
     ctx->stats.kernel_launches += 1;
   } else {
@@ -460,6 +483,9 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   GW_TRY(cudaMemcpyAsync(h_fc.data(), d_fc, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost,
                          ctx->stream));
   GW_TRY(cudaStreamSynchronize(ctx->stream));
+  float ms_ck = 0.f;
+  GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
+  ctx->stats.ms_step_c_kernel += ms_ck;
   long long act = 0, sl_act = 0;
   for (int c : h_counts) {
     act += c > 0;
@@ -521,6 +547,8 @@ void gw_destroy(gw_ctx* ctx) {
   free_dev(ctx->d_ri_off);
   free_dev(ctx->d_atom_of_ri);
   free_dev(ctx->d_atom_of_ao);
+  for (cudaEvent_t e : c_events(ctx)) cudaEventDestroy(e);
+  c_events(ctx).clear();
   auto& reg = work_registry();
   auto it = reg.find(ctx);
   if (it != reg.end()) {
@@ -785,11 +813,12 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     GW_TRY(cudaMemsetAsync(acc, 0, (size_t)nri * nri * sizeof(double), ctx->stream));
     GW_TRY(cudaEventRecord(ev[1], ctx->stream));
     std::vector<double> fc;
-    for (const Batch& b : batches) {
+    for (size_t bi = 0; bi < batches.size(); ++bi) {
+      const Batch& b = batches[bi];
       if (f64)
-        rc = chi_one_batch<double>(ctx, b, go, gv, ctx->d_panel64, thr, acc, fc, precision);
+        rc = chi_one_batch<double>(ctx, b, go, gv, ctx->d_panel64, thr, acc, fc, precision, bi);
       else
-        rc = chi_one_batch<float>(ctx, b, go32, gv32, ctx->d_panel32, thr, acc, fc, precision);
+        rc = chi_one_batch<float>(ctx, b, go32, gv32, ctx->d_panel32, thr, acc, fc, precision, bi);
       if (rc) return rc;
     }
     GW_TRY(cudaEventRecord(ev[2], ctx->stream));

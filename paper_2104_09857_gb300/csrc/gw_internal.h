@@ -95,7 +95,7 @@ struct gw_ctx {
   long long lam_total = 0;
 
   // options
-  double batch_bytes = 24e9;
+  double batch_bytes = 64e9;
   int batch_atoms = 0;
 
   gw_stats stats{};

@@ -118,6 +118,29 @@ int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
 int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
                int screening, double* chi_out, int out_on_device);
 
+/* chi_PQ(i tau) for one tau point in FP64 without allocating device memory.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc when they need chi -- a host framework whose caching
+ * allocator owns the device memory budget and must not see allocations behind
+ * its back, a process that reserved all device memory up front, or
+ * latency-bound code that cannot afford the implicit device synchronisation
+ * of cudaMalloc/cudaFree.  Same result as gw_chi_tau(tau_index, 1, thr,
+ * GW_FP64, GW_SCREEN_BOUND) up to summation order.
+ *
+ * Every per-call work buffer lives in one fixed 64 MiB array of device
+ * global memory inside the library (held on each GPU that loads the library
+ * until the process exits).  Systems whose Green's functions, chi and the
+ * operands of one single-sigma-atom batch do not fit are rejected with
+ * GW_ERR_INVALID_ARG and a message giving the bytes needed.  The tensor
+ * panels depend on thr and are built by gw_chi_tau: call it once with the same
+ * thr first (GW_ERR_ORDER otherwise).  The first call on a device looks up
+ * the array's device address and must come before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps race and corrupt each
+ * other's results.  chi_out_device: [n_ri_total][n_ri_total] FP64 on the
+ * context's device.  Runs on the context's stream and returns after it has
+ * drained.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double* chi_out_device);
+
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
 

@@ -83,6 +83,7 @@ SIGNATURES = [
     ("gw_chi_tau", _I, [_P, _I, _I, _D, _I, _I, _P, _I]),
     ("gw_get_stats", _I, [_P, ctypes.POINTER(gw_stats)]),
     ("gw_set_option", _I, [_P, ctypes.c_char_p, _D]),
+    ("gw_chi_tau_noalloc", _I, [_P, _I, _D, _P]),
 ]
 
 
@@ -160,6 +161,12 @@ def gw_chi_tau(ctx: int, tau_first: int, tau_count: int, thr: float, precision: 
                screening: int, out_ptr: int, out_on_device: bool) -> None:
     _check(ctx, lib().gw_chi_tau(ctx, tau_first, tau_count, float(thr), precision, screening,
                                  out_ptr, int(bool(out_on_device))))
+
+
+def gw_chi_tau_noalloc(ctx: int, tau_index: int, thr: float, out_ptr: int) -> None:
+    """FP64 chi for one tau point into a device buffer, with no device
+    allocation inside the library (fixed work array; see include/gwchi.h)."""
+    _check(ctx, lib().gw_chi_tau_noalloc(ctx, int(tau_index), float(thr), out_ptr))
 
 
 def gw_get_stats(ctx: int) -> dict:

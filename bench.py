@@ -374,7 +374,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3", "bf16x6", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "bf16x6", "fp64"], default="bf16x6")
     ap.add_argument("--fp64-taus", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=1)

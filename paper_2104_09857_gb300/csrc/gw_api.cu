@@ -21,6 +21,7 @@
 
 #include "gw_internal.h"
 #include "k_simt.h"
+#include "k_tc.h"
 
 using gw::Batch;
 using gw::kSlabAO;
@@ -399,8 +400,11 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   ctx->stats.bytes_operands += (double)(prow + ctx->nri) * Kb * sizeof(T);
 
   // block filter of X and Y, occupancy flags
+  const bool tcpath = precision == GW_BF16X3 || precision == GW_BF16X6;
+  const int slices = precision == GW_BF16X6 ? 3 : 2;
+  const int tile = tcpath ? gw::tc_tile_rows() : 64;
   const int nslab = b.nslab;
-  const int npt = (prow + 63) / 64, nqt = (ctx->nri + 63) / 64;
+  const int npt = (prow + tile - 1) / tile, nqt = (ctx->nri + tile - 1) / tile;
   const int pa0 = [&] {
     int a = 0;
     while (ctx->ri_off[a + 1] <= b.P0) ++a;
@@ -421,11 +425,11 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   int* d_nao;
   if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao))) return rc;
   gw::launch_operand_block_filter<T>(X, Kb, b.P0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns,
-                                     d_seg, pa0, npa, ctx->n_at, thr, ctx->naop, bx, fx, npt,
+                                     d_seg, pa0, npa, ctx->n_at, thr, ctx->naop, bx, fx, npt, tile,
                                      ctx->stream);
   GW_CHECK_LAUNCH();
   gw::launch_operand_block_filter<T>(Y, Kb, 0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns, d_seg,
-                                     0, ctx->n_at, ctx->n_at, thr, ctx->naop, by, fy, nqt,
+                                     0, ctx->n_at, ctx->n_at, thr, ctx->naop, by, fy, nqt, tile,
                                      ctx->stream);
   GW_CHECK_LAUNCH();
   // slabs
@@ -448,7 +452,7 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
   if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
   gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, ctx->nri, ctx->d_atom_of_ri, d_len,
-                         tasks, counts, kacc, ctx->stream);
+                         tasks, counts, kacc, tile, ctx->stream);
   GW_CHECK_LAUNCH();
   double* d_fc;
   if ((rc = wsT(ctx, "fc", (size_t)ns * ctx->n_at, &d_fc))) return rc;
@@ -461,7 +465,9 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   // step C
   cudaEvent_t ec0, ec1;
   if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
-  if (precision == GW_FP64 || precision == GW_FP32) {
+  std::vector<int> h_counts((size_t)npt * nqt);
+  int* d_err = nullptr;
+  if (!tcpath) {
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     gw::launch_chi_tiles<T, T>(X, Y, Kb, b.P0, prow, ctx->nri, tasks, counts, nslab, npt, nqt, d_k0,
                                d_len, acc, ctx->stream);
@@ -470,10 +476,43 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
     ctx->stats.c_launches += 1;
     ctx->stats.kernel_launches += 1;
   } else {
-    return fail(ctx, GW_ERR_UNSUPPORTED, "tensor-core step C requires the FP32 operand route");
+    if (sizeof(T) != sizeof(float))
+      return fail(ctx, GW_ERR_INVALID_ARG, "tensor-core step C needs FP32 operands");
+    // split X and Y into bf16 slices [slices][rows][Kb]
+    void *xs, *ys;
+    if ((rc = ws(ctx, "Xs", (size_t)slices * prow * Kb * 2, &xs))) return rc;
+    if ((rc = ws(ctx, "Ys", (size_t)slices * ctx->nri * Kb * 2, &ys))) return rc;
+    gw::launch_split_bf16(slices, reinterpret_cast<const float*>(X), xs, (long long)prow * Kb,
+                          ctx->stream);
+    gw::launch_split_bf16(slices, reinterpret_cast<const float*>(Y), ys, (long long)ctx->nri * Kb,
+                          ctx->stream);
+    GW_CHECK_LAUNCH();
+    ctx->stats.kernel_launches += 2;
+    CUtensorMap mx, my;
+    if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile) ||
+        gw::make_slice_map(&my, ys, Kb, ctx->nri, slices, tile))
+      return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
+    // active tiles
+    GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    GW_TRY(cudaStreamSynchronize(ctx->stream));
+    std::vector<int> active;
+    for (size_t t = 0; t < h_counts.size(); ++t)
+      if (h_counts[t] > 0) active.push_back((int)t);
+    int* d_active;
+    if ((rc = upload(ctx, "active_tiles", active, &d_active))) return rc;
+    if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
+    GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+    GW_TRY(cudaEventRecord(ec0, ctx->stream));
+    if (gw::launch_chi_tc(slices, mx, my, d_active, (int)active.size(), tasks, counts, nslab, d_k0,
+                          d_len, b.P0, prow, ctx->nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
+      return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+    GW_CHECK_LAUNCH();
+    GW_TRY(cudaEventRecord(ec1, ctx->stream));
+    ctx->stats.c_launches += 1;
+    ctx->stats.kernel_launches += 1;
   }
   // counters (small D2H)
-  std::vector<int> h_counts((size_t)npt * nqt);
   std::vector<long long> h_kacc((size_t)npt * nqt);
   std::vector<double> h_fc((size_t)ns * ctx->n_at);
   GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
@@ -482,7 +521,12 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
                          cudaMemcpyDeviceToHost, ctx->stream));
   GW_TRY(cudaMemcpyAsync(h_fc.data(), d_fc, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost,
                          ctx->stream));
+  int h_err = 0;
+  if (d_err) GW_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   GW_TRY(cudaStreamSynchronize(ctx->stream));
+  if (h_err)
+    return fail(ctx, GW_ERR_TIMEOUT,
+                "tensor-core step C: a bounded wait gave up (flags " + std::to_string(h_err) + ")");
   float ms_ck = 0.f;
   GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
   ctx->stats.ms_step_c_kernel += ms_ck;
@@ -496,10 +540,11 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   ctx->stats.slabs_total += (long long)npt * nqt * nslab;
   ctx->stats.slabs_active += sl_act;
   for (double v : h_fc) fc_host.push_back(v);
-  // issued by step C: 2 * tile area * K over active tiles
+  // issued by step C: 2 * tile area * K over active tiles (x products per product)
   double ksum = 0.0;
   for (long long k : h_kacc) ksum += (double)k;
-  ctx->stats.flops_issued += 2.0 * 64.0 * 64.0 * ksum;
+  const double prods = tcpath ? (slices == 3 ? 6.0 : 3.0) : 1.0;
+  ctx->stats.flops_issued += 2.0 * tile * tile * ksum * prods;
   return GW_OK;
 }
 
@@ -723,6 +768,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->batch_bytes = value;
     return GW_OK;
   }
+  if (!strcmp(key, "flush_k")) {
+    if (!(value >= 64 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [64, 2^30]");
+    ctx->flush_k = (int)value;
+    return GW_OK;
+  }
   if (!strcmp(key, "batch_atoms")) {
     if (!(value >= 0)) return fail(ctx, GW_ERR_INVALID_ARG, "batch_atoms must be >= 0");
     ctx->batch_atoms = (int)value;
@@ -762,7 +812,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   const bool f64 = precision == GW_FP64;
   if (!f64 && (rc = ensure_panel32(ctx))) return rc;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;
-  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  // device bytes per operand element: FP64, FP32, or FP32 plus bf16 slices
+  const size_t esz = f64 ? sizeof(double)
+                         : sizeof(float) + (precision == GW_BF16X6 ? 6 : precision == GW_BF16X3 ? 4 : 0);
   std::vector<Batch> batches = plan_batches(ctx, esz, ctx->batch_bytes);
   ctx->stats.n_batches = (int)batches.size();
 

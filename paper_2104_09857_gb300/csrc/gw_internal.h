@@ -97,6 +97,7 @@ struct gw_ctx {
   // options
   double batch_bytes = 64e9;
   int batch_atoms = 0;
+  int flush_k = 256;  // tensor-core step C: FP32 accumulator drained every flush_k elements
 
   gw_stats stats{};
 };

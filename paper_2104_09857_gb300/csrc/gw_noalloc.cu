@@ -350,12 +350,12 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
     int pa1 = pa0;
     while (pa1 < n_at && ctx->ri_off[pa1] < b.P1) ++pa1;
     gw::launch_operand_block_filter<double>(X, Kb, b.P0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns,
-                                            d_seg, pa0, pa1 - pa0, n_at, thr, naop, bx, fx, npt, st);
+                                            d_seg, pa0, pa1 - pa0, n_at, thr, naop, bx, fx, npt, 64, st);
     gw::launch_operand_block_filter<double>(Y, Kb, 0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns,
-                                            d_seg, 0, n_at, n_at, thr, naop, by, fy, nqt, st);
+                                            d_seg, 0, n_at, n_at, thr, naop, by, fy, nqt, 64, st);
     NA_LAUNCHED();
     gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
-                           counts, kacc, st);
+                           counts, kacc, 64, st);
     gw::launch_chi_tiles<double, double>(X, Y, Kb, b.P0, prow, nri, tasks, counts, nslab, npt, nqt,
                                          d_k0, d_len, acc, st);
     NA_LAUNCHED();

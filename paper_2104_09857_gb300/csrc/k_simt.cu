@@ -341,7 +341,8 @@ __global__ void k_operand_block_filter(T* __restrict__ Z, long long ldk, int row
                                        const int* __restrict__ n_ao, int s0, int ns,
                                        const long long* __restrict__ seg, int pa0, int npa, int n_at,
                                        double thr, int naop, unsigned char* __restrict__ blockflag,
-                                       unsigned char* __restrict__ tileflag, int ntile) {
+                                       unsigned char* __restrict__ tileflag, int ntile,
+                                       int tile_rows) {
   long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   long long nblk = (long long)ns * n_at * npa;
@@ -376,7 +377,7 @@ __global__ void k_operand_block_filter(T* __restrict__ Z, long long ldk, int row
   if (lane == 0) blockflag[w] = nz;
   if (nz) {
     int cs = ao_off[m] / kSlabAO, ce = (ao_off[m + 1] - 1) / kSlabAO;
-    int ts = rows0 / 64, te = (rows0 + nrows - 1) / 64;
+    int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
     int nsl = naop / kSlabAO;
     for (int c = cs + lane; c <= ce; c += 32)
       for (int tt = ts; tt <= te; ++tt) tileflag[((long long)sl * nsl + c) * ntile + tt] = 1;
@@ -390,11 +391,11 @@ __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsign
                               int nslab, int npt, int nqt, int P0, int prow, int nri,
                               const int* __restrict__ atom_of_ri, const int* __restrict__ slab_len,
                               int* __restrict__ tasks, int* __restrict__ counts,
-                              long long* __restrict__ kacc) {
+                              long long* __restrict__ kacc, int tile_rows) {
   int tile = blockIdx.x;
   int pt = tile / nqt, qt = tile % nqt;
-  int pfirst = P0 + pt * 64;
-  int qlast = min(nri, (qt + 1) * 64) - 1;
+  int pfirst = P0 + pt * tile_rows;
+  int qlast = min(nri, (qt + 1) * tile_rows) - 1;
   bool upper = atom_of_ri[pfirst] <= atom_of_ri[qlast];
   // warp-serial compaction in slab order (deterministic)
   if (threadIdx.x >= 32) return;
@@ -520,28 +521,28 @@ void launch_operand_block_filter(T* Z, long long ldk, int rowoff, const int* ri_
                                  const int* ao_off, const int* n_ao, int s0, int ns,
                                  const long long* seg, int pa0, int npa, int n_at, double thr,
                                  int naop, unsigned char* blockflag, unsigned char* tileflag,
-                                 int ntile, cudaStream_t st) {
+                                 int ntile, int tile_rows, cudaStream_t st) {
   long long nblk = (long long)ns * n_at * npa;
   if (nblk == 0) return;
   k_operand_block_filter<T><<<(unsigned)((nblk + 7) / 8), 256, 0, st>>>(
       Z, ldk, rowoff, ri_off, ao_off, n_ao, s0, ns, seg, pa0, npa, n_at, thr, naop, blockflag,
-      tileflag, ntile);
+      tileflag, ntile, tile_rows);
 }
 template void launch_operand_block_filter<double>(double*, long long, int, const int*, const int*,
                                                   const int*, int, int, const long long*, int, int,
                                                   int, double, int, unsigned char*, unsigned char*,
-                                                  int, cudaStream_t);
+                                                  int, int, cudaStream_t);
 template void launch_operand_block_filter<float>(float*, long long, int, const int*, const int*,
                                                  const int*, int, int, const long long*, int, int,
                                                  int, double, int, unsigned char*, unsigned char*,
-                                                 int, cudaStream_t);
+                                                 int, int, cudaStream_t);
 
 void launch_build_tasks(const unsigned char* fx, const unsigned char* fy, int nslab, int npt,
                         int nqt, int P0, int prow, int nri, const int* atom_of_ri,
                         const int* slab_len, int* tasks, int* counts, long long* kacc,
-                        cudaStream_t st) {
+                        int tile_rows, cudaStream_t st) {
   k_build_tasks<<<npt * nqt, 32, 0, st>>>(fx, fy, nslab, npt, nqt, P0, prow, nri, atom_of_ri,
-                                          slab_len, tasks, counts, kacc);
+                                          slab_len, tasks, counts, kacc, tile_rows);
 }
 
 void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int n_at, int pa0,

@@ -191,3 +191,45 @@ def test_errors_order_and_arguments(lib):
         assert e.value.code == -1
         out = ctx.chi_tau(0.0, "fp64", 0, 1)
         assert torch.isfinite(out).all()
+
+
+# ---------------------------------------------------------------------------
+# tensor-core split-BF16 forms
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,thr", [("benzene", 0.0), ("ribbon28", 1e-9), ("ribbon28", 1e-3)])
+def test_bf16x6_matches_oracle(lib, name, thr):
+    """Three-slice split, 6 products: within the 1e-6 mixed-precision bar."""
+    case = make_case(name, n_tau=4)
+    got, st = _run(lib, case, precision="bf16x6", thr=thr)
+    ref = oc.chi_dense(case, thr=thr)
+    _check(got, ref, TOL["bf16x6"])
+    assert st["c_launches"] > 0
+
+
+def _rel_err(got, ref):
+    return max(np.linalg.norm(g - r) / np.linalg.norm(r) for g, r in zip(got, ref))
+
+
+def test_bf16x6_many_batches_ragged_tiles_and_flush(lib):
+    """Ragged 128-row tiles over one- and five-atom batches; the accuracy bar
+    holds for accumulator drains every 64..256 reduction elements.  Draining
+    rarely (4096) lets the tensor cores' FP32 accumulation error grow, which
+    is why the default is 256."""
+    case = make_case("ribbon28", n_tau=2)
+    ref = oc.chi_dense(case)
+    for atoms, flush in ((1, 64), (5, 128), (0, 256)):
+        got, _ = _run(lib, case, precision="bf16x6", options={"batch_atoms": atoms, "flush_k": flush})
+        _check(got, ref, TOL["bf16x6"])
+    e_short = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 64})[0], ref)
+    e_long = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 4096})[0], ref)
+    assert e_long > e_short
+
+
+def test_bf16x3_error_is_split_limited(lib):
+    """Two-slice split, 3 products: the dropped low-low product and the 16-bit
+    representation bound the error near 2^-17; it does not meet 1e-6."""
+    case = make_case("benzene", n_tau=4)
+    got, _ = _run(lib, case, precision="bf16x3")
+    ref = oc.chi_dense(case)
+    _check(got, ref, 2e-5)

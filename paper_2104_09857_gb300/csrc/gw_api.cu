@@ -131,6 +131,9 @@ void reset_tensor(gw_ctx* ctx) {
   ctx->blk_norm.clear();
   ctx->panels_ok = false;
   ctx->panel32_ok = false;
+  free_dev(ctx->d_pt);
+  ctx->d_pt = nullptr;
+  ctx->pt_ok = false;
 }
 
 void reset_greens(gw_ctx* ctx) {
@@ -244,6 +247,7 @@ int build_panels(gw_ctx* ctx, double thr) {
   GW_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->panels_ok = true;
   ctx->panels_thr = thr;
+  ctx->pt_ok = false;
   return GW_OK;
 }
 
@@ -400,9 +404,9 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   ctx->stats.bytes_operands += (double)(prow + ctx->nri) * Kb * sizeof(T);
 
   // block filter of X and Y, occupancy flags
-  const bool tcpath = precision == GW_BF16X3 || precision == GW_BF16X6;
-  const int slices = precision == GW_BF16X6 ? 3 : 2;
-  const int tile = tcpath ? gw::tc_tile_rows() : 64;
+  const bool tcpath = false;
+  const int slices = 1;
+  const int tile = 64;
   const int nslab = b.nslab;
   const int npt = (prow + tile - 1) / tile, nqt = (ctx->nri + tile - 1) / tile;
   const int pa0 = [&] {
@@ -467,46 +471,10 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
   std::vector<int> h_counts((size_t)npt * nqt);
   int* d_err = nullptr;
-  if (!tcpath) {
+  {
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     gw::launch_chi_tiles<T, T>(X, Y, Kb, b.P0, prow, ctx->nri, tasks, counts, nslab, npt, nqt, d_k0,
                                d_len, acc, ctx->stream);
-    GW_CHECK_LAUNCH();
-    GW_TRY(cudaEventRecord(ec1, ctx->stream));
-    ctx->stats.c_launches += 1;
-    ctx->stats.kernel_launches += 1;
-  } else {
-    if (sizeof(T) != sizeof(float))
-      return fail(ctx, GW_ERR_INVALID_ARG, "tensor-core step C needs FP32 operands");
-    // split X and Y into bf16 slices [slices][rows][Kb]
-    void *xs, *ys;
-    if ((rc = ws(ctx, "Xs", (size_t)slices * prow * Kb * 2, &xs))) return rc;
-    if ((rc = ws(ctx, "Ys", (size_t)slices * ctx->nri * Kb * 2, &ys))) return rc;
-    gw::launch_split_bf16(slices, reinterpret_cast<const float*>(X), xs, (long long)prow * Kb,
-                          ctx->stream);
-    gw::launch_split_bf16(slices, reinterpret_cast<const float*>(Y), ys, (long long)ctx->nri * Kb,
-                          ctx->stream);
-    GW_CHECK_LAUNCH();
-    ctx->stats.kernel_launches += 2;
-    CUtensorMap mx, my;
-    if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile) ||
-        gw::make_slice_map(&my, ys, Kb, ctx->nri, slices, tile))
-      return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
-    // active tiles
-    GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
-                           cudaMemcpyDeviceToHost, ctx->stream));
-    GW_TRY(cudaStreamSynchronize(ctx->stream));
-    std::vector<int> active;
-    for (size_t t = 0; t < h_counts.size(); ++t)
-      if (h_counts[t] > 0) active.push_back((int)t);
-    int* d_active;
-    if ((rc = upload(ctx, "active_tiles", active, &d_active))) return rc;
-    if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
-    GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
-    GW_TRY(cudaEventRecord(ec0, ctx->stream));
-    if (gw::launch_chi_tc(slices, mx, my, d_active, (int)active.size(), tasks, counts, nslab, d_k0,
-                          d_len, b.P0, prow, ctx->nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
-      return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
     GW_CHECK_LAUNCH();
     GW_TRY(cudaEventRecord(ec1, ctx->stream));
     ctx->stats.c_launches += 1;
@@ -543,8 +511,311 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   // issued by step C: 2 * tile area * K over active tiles (x products per product)
   double ksum = 0.0;
   for (long long k : h_kacc) ksum += (double)k;
-  const double prods = tcpath ? (slices == 3 ? 6.0 : 3.0) : 1.0;
-  ctx->stats.flops_issued += 2.0 * tile * tile * ksum * prods;
+  (void)tcpath;
+  (void)slices;
+  ctx->stats.flops_issued += 2.0 * tile * tile * ksum;
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core route: transposed split panels (once per thr and slice count)
+// ---------------------------------------------------------------------------
+int ensure_pt(gw_ctx* ctx, int slices) {
+  if (ctx->pt_ok && ctx->pt_slices == slices && ctx->pt_thr == ctx->panels_thr) return GW_OK;
+  free_dev(ctx->d_pt);
+  ctx->d_pt = nullptr;
+  ctx->pt_ok = false;
+  ctx->pt_tasks.assign(ctx->n_at, gw::PanelTaskTC{});
+  std::vector<gw::PanelTaskTC> list;
+  long long rows = 0;
+  int kmax = 64, max_npad = 0;
+  for (int s = 0; s < ctx->n_at; ++s) {
+    const PanelDesc& d = ctx->panels[s];
+    gw::PanelTaskTC t{};
+    t.K = d.K;
+    if (d.K == 0) {
+      ctx->pt_tasks[s] = t;
+      continue;
+    }
+    t.panel_off = d.off;
+    t.N = d.npw * d.nsig;
+    t.npw = d.npw;
+    t.nsig = d.nsig;
+    t.p0 = d.p0;
+    t.aom = ctx->ao_off[s];
+    t.owner = s;
+    t.lam_off = d.lam_off;
+    t.ksteps = (d.K + 63) / 64;
+    t.p_row0 = (int)rows;
+    const int npad = (t.N + 127) / 128 * 128;
+    rows += npad;
+    max_npad = std::max(max_npad, npad);
+    kmax = std::max(kmax, t.ksteps * 64);
+    ctx->pt_tasks[s] = t;
+    list.push_back(t);
+  }
+  if (rows > INT32_MAX) return fail(ctx, GW_ERR_INVALID_ARG, "transposed panels exceed 2^31 rows");
+  const size_t bytes = (size_t)slices * rows * kmax * 2;
+  GW_TRY(cudaMalloc(&ctx->d_pt, std::max<size_t>(bytes, 16)));
+  gw::PanelTaskTC* d_list;
+  int rc;
+  if ((rc = upload(ctx, "pt_list", list, &d_list))) return rc;
+  gw::launch_transpose_panels(ctx->d_panel64, d_list, (int)list.size(), max_npad, kmax, slices,
+                              rows * kmax, ctx->d_pt, ctx->stream);
+  GW_CHECK_LAUNCH();
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->pt_rows = rows;
+  ctx->pt_kmax = kmax;
+  ctx->pt_slices = slices;
+  ctx->pt_thr = ctx->panels_thr;
+  ctx->pt_ok = true;
+  return GW_OK;
+}
+
+// One batch on the tensor cores: steps A and B straight into bf16 slices,
+// block filter from the accumulated norms, task lists, step C.
+int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const double* g_virt,
+                     double thr, double* acc, std::vector<double>& fc_host, int precision,
+                     size_t batch_idx) {
+  const int slices = precision == GW_BF16X6 ? 3 : 2;
+  const double prods = slices == 3 ? 6.0 : 3.0;
+  const int tile = gw::tc_tile_rows();
+  const int ns = b.s1 - b.s0;
+  const int prow = b.P1 - b.P0;
+  const long long Kb = b.Kb;
+  const int n_at = ctx->n_at, nri = ctx->nri, nao = ctx->nao;
+  int rc;
+  if (prow == 0 || Kb == 0) return GW_OK;
+  const int kmax = ctx->pt_kmax;
+  void *xs, *ys;
+  if ((rc = ws(ctx, "Xs", (size_t)slices * prow * Kb * 2, &xs))) return rc;
+  if ((rc = ws(ctx, "Ys", (size_t)slices * nri * Kb * 2, &ys))) return rc;
+  GW_TRY(cudaMemsetAsync(xs, 0, (size_t)slices * prow * Kb * 2, ctx->stream));
+  GW_TRY(cudaMemsetAsync(ys, 0, (size_t)slices * nri * Kb * 2, ctx->stream));
+  const int pa0 = [&] {
+    int a = 0;
+    while (ctx->ri_off[a + 1] <= b.P0) ++a;
+    return a;
+  }();
+  int pa1 = pa0;
+  while (pa1 < n_at && ctx->ri_off[pa1] < b.P1) ++pa1;
+  const int npa = pa1 - pa0;
+  float *bx2, *by2;
+  if ((rc = wsT(ctx, "bx2", (size_t)ns * n_at * npa, &bx2))) return rc;
+  if ((rc = wsT(ctx, "by2", (size_t)ns * n_at * n_at, &by2))) return rc;
+  GW_TRY(cudaMemsetAsync(bx2, 0, (size_t)ns * n_at * npa * sizeof(float), ctx->stream));
+  GW_TRY(cudaMemsetAsync(by2, 0, (size_t)ns * n_at * n_at * sizeof(float), ctx->stream));
+  int* d_err;
+  if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
+  GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+  CUtensorMap mp;
+  if (gw::make_slice_map(&mp, ctx->d_pt, kmax, ctx->pt_rows, slices, tile))
+    return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
+  double issued = 0.0;
+  cudaEvent_t ea0, ea1;
+  if ((rc = c_event_pair(ctx, 1000 + batch_idx, &ea0, &ea1))) return rc;
+  GW_TRY(cudaEventRecord(ea0, ctx->stream));
+
+  // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu ----
+  {
+    const int rows_a = (nao + tile - 1) / tile * tile;
+    std::vector<gw::PanelTaskTC> ta;
+    std::vector<int4> tiles;
+    for (int s = b.s0; s < b.s1; ++s) {
+      gw::PanelTaskTC t = ctx->pt_tasks[s];
+      if (t.K == 0) continue;
+      t.g_row0 = (int)ta.size() * rows_a;
+      t.seg = b.seg[s - b.s0];
+      t.s_local = s - b.s0;
+      const int ntn = (t.N + tile - 1) / tile;
+      for (int mt = 0; mt < rows_a / tile; ++mt)
+        for (int nt = 0; nt < ntn; ++nt) tiles.push_back(make_int4((int)ta.size(), mt, nt, 0));
+      issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+      ta.push_back(t);
+    }
+    if (!ta.empty()) {
+      gw::PanelTaskTC* d_ta;
+      int4* d_tiles;
+      void* gg;
+      if ((rc = upload(ctx, "tc_tasksA", ta, &d_ta))) return rc;
+      if ((rc = upload(ctx, "tc_tilesA", tiles, &d_tiles))) return rc;
+      const long long g_elems = (long long)ta.size() * rows_a * kmax;
+      if ((rc = ws(ctx, "GgA", (size_t)slices * g_elems * 2, &gg))) return rc;
+      gw::launch_gather_g(g_occ, nao, d_ta, (int)ta.size(), ctx->d_lam, 0, nao, rows_a, kmax, slices,
+                          g_elems, gg, ctx->stream);
+      GW_CHECK_LAUNCH();
+      CUtensorMap mg;
+      if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile))
+        return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step A)");
+      if (gw::launch_panel_tc(slices, mg, mp, d_tiles, (int)tiles.size(), d_ta, 0, nao, xs,
+                              (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
+                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, n_at, npa, pa0, ctx->flush_k,
+                              d_err, ctx->stream))
+        return fail(ctx, GW_ERR_CUDA, "tensor-core step A launch setup failed");
+      GW_CHECK_LAUNCH();
+      ctx->stats.kernel_launches += 2;
+    }
+  }
+  // ---- step B: Y[Q][(s, mu, s')] for every panel, rows sigma of the batch ----
+  {
+    const int r0 = ctx->ao_off[b.s0];
+    const int R = ctx->ao_off[b.s1] - r0;
+    const int rows_b = (R + tile - 1) / tile * tile;
+    std::vector<gw::PanelTaskTC> tb;
+    std::vector<int4> tiles;
+    for (int m = 0; m < n_at; ++m) {
+      gw::PanelTaskTC t = ctx->pt_tasks[m];
+      if (t.K == 0) continue;
+      t.g_row0 = (int)tb.size() * rows_b;
+      const int ntn = (t.N + tile - 1) / tile;
+      for (int mt = 0; mt < rows_b / tile; ++mt)
+        for (int nt = 0; nt < ntn; ++nt) tiles.push_back(make_int4((int)tb.size(), mt, nt, 0));
+      issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_b / tile) * ntn;
+      tb.push_back(t);
+    }
+    std::vector<long long> rowbase(R);
+    std::vector<int> rowmul(R), rowsl(R);
+    for (int s = b.s0; s < b.s1; ++s)
+      for (int i = 0; i < ctx->n_ao[s]; ++i) {
+        rowbase[ctx->ao_off[s] - r0 + i] = b.seg[s - b.s0] + i;
+        rowmul[ctx->ao_off[s] - r0 + i] = ctx->n_ao[s];
+        rowsl[ctx->ao_off[s] - r0 + i] = s - b.s0;
+      }
+    if (!tb.empty() && R > 0) {
+      gw::PanelTaskTC* d_tb;
+      int4* d_tiles;
+      long long* d_rowbase;
+      int *d_rowmul, *d_rowsl;
+      void* gg;
+      if ((rc = upload(ctx, "tc_tasksB", tb, &d_tb))) return rc;
+      if ((rc = upload(ctx, "tc_tilesB", tiles, &d_tiles))) return rc;
+      if ((rc = upload(ctx, "rowbase", rowbase, &d_rowbase))) return rc;
+      if ((rc = upload(ctx, "rowmul", rowmul, &d_rowmul))) return rc;
+      if ((rc = upload(ctx, "rowsl", rowsl, &d_rowsl))) return rc;
+      const long long g_elems = (long long)tb.size() * rows_b * kmax;
+      if ((rc = ws(ctx, "GgB", (size_t)slices * g_elems * 2, &gg))) return rc;
+      gw::launch_gather_g(g_virt, nao, d_tb, (int)tb.size(), ctx->d_lam, r0, R, rows_b, kmax, slices,
+                          g_elems, gg, ctx->stream);
+      GW_CHECK_LAUNCH();
+      CUtensorMap mg;
+      if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile))
+        return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
+      if (gw::launch_panel_tc(slices, mg, mp, d_tiles, (int)tiles.size(), d_tb, 1, R, ys,
+                              (long long)nri * Kb, Kb, 0, d_rowbase, d_rowmul, d_rowsl, by2,
+                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, n_at, n_at, 0, ctx->flush_k,
+                              d_err, ctx->stream))
+        return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
+      GW_CHECK_LAUNCH();
+      ctx->stats.kernel_launches += 2;
+    }
+  }
+  GW_TRY(cudaEventRecord(ea1, ctx->stream));
+  ctx->stats.bytes_operands += (double)(prow + nri) * Kb * 2.0 * slices;
+
+  // ---- block filter, occupancy, task lists ----
+  const int nslab = b.nslab;
+  const int npt = (prow + tile - 1) / tile, nqt = (nri + tile - 1) / tile;
+  unsigned char *bx, *by, *fx, *fy;
+  if ((rc = wsT(ctx, "bx", (size_t)ns * n_at * npa, &bx))) return rc;
+  if ((rc = wsT(ctx, "by", (size_t)ns * n_at * n_at, &by))) return rc;
+  if ((rc = wsT(ctx, "fx", (size_t)nslab * npt, &fx))) return rc;
+  if ((rc = wsT(ctx, "fy", (size_t)nslab * nqt, &fy))) return rc;
+  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)nslab * npt, ctx->stream));
+  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)nslab * nqt, ctx->stream));
+  long long* d_seg;
+  int* d_nao;
+  if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
+  if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao))) return rc;
+  gw::launch_slices_block_filter(xs, slices, (long long)prow * Kb, Kb, b.P0, ctx->d_ri_off,
+                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, pa0, npa, n_at, thr,
+                                 ctx->naop, bx2, bx, fx, npt, tile, ctx->stream);
+  gw::launch_slices_block_filter(ys, slices, (long long)nri * Kb, Kb, 0, ctx->d_ri_off, ctx->d_ao_off,
+                                 d_nao, b.s0, ns, d_seg, 0, n_at, n_at, thr, ctx->naop, by2, by, fy,
+                                 nqt, tile, ctx->stream);
+  GW_CHECK_LAUNCH();
+  std::vector<long long> slab_k0(nslab);
+  std::vector<int> slab_len(nslab);
+  const int per = ctx->naop / kSlabAO;
+  for (int sl = 0; sl < ns; ++sl)
+    for (int c = 0; c < per; ++c) {
+      const int nsig = ctx->n_ao[b.s0 + sl];
+      slab_k0[sl * per + c] = b.seg[sl] + (long long)c * kSlabAO * nsig;
+      slab_len[sl * per + c] = kSlabAO * nsig;
+    }
+  long long* d_k0;
+  int* d_len;
+  if ((rc = upload(ctx, "slab_k0", slab_k0, &d_k0))) return rc;
+  if ((rc = upload(ctx, "slab_len", slab_len, &d_len))) return rc;
+  int *tasks, *counts;
+  long long* kacc;
+  if ((rc = wsT(ctx, "tasks", (size_t)npt * nqt * nslab, &tasks))) return rc;
+  if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
+  if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
+  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
+                         counts, kacc, tile, ctx->stream);
+  double* d_fc;
+  int* d_nri;
+  if ((rc = wsT(ctx, "fc", (size_t)ns * n_at, &d_fc))) return rc;
+  if ((rc = upload(ctx, "n_ri_b", ctx->n_ri, &d_nri))) return rc;
+  gw::launch_count_c(bx, by, ns, n_at, pa0, npa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
+  GW_CHECK_LAUNCH();
+  ctx->stats.kernel_launches += 4;
+  std::vector<int> h_counts((size_t)npt * nqt);
+  std::vector<long long> h_kacc((size_t)npt * nqt);
+  GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaMemcpyAsync(h_kacc.data(), kacc, h_kacc.size() * sizeof(long long),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  // active tiles, longest first (static round-robin over persistent CTAs)
+  std::vector<int> active;
+  for (size_t t = 0; t < h_counts.size(); ++t)
+    if (h_counts[t] > 0) active.push_back((int)t);
+  std::stable_sort(active.begin(), active.end(),
+                   [&](int a, int c) { return h_kacc[a] > h_kacc[c]; });
+  int* d_active;
+  if ((rc = upload(ctx, "active_tiles", active, &d_active))) return rc;
+  CUtensorMap mx, my;
+  if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile) ||
+      gw::make_slice_map(&my, ys, Kb, nri, slices, tile))
+    return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
+  cudaEvent_t ec0, ec1;
+  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
+  GW_TRY(cudaEventRecord(ec0, ctx->stream));
+  if (gw::launch_chi_tc(slices, mx, my, d_active, (int)active.size(), tasks, counts, nslab, d_k0,
+                        d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
+    return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+  GW_CHECK_LAUNCH();
+  GW_TRY(cudaEventRecord(ec1, ctx->stream));
+  ctx->stats.c_launches += 1;
+  ctx->stats.kernel_launches += 1;
+  std::vector<double> h_fc((size_t)ns * n_at);
+  int h_err = 0;
+  GW_TRY(cudaMemcpyAsync(h_fc.data(), d_fc, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  GW_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
+  if (h_err)
+    return fail(ctx, GW_ERR_TIMEOUT,
+                "tensor-core kernel: a bounded wait gave up (flags " + std::to_string(h_err) + ")");
+  float ms_ck = 0.f, ms_ab = 0.f;
+  GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
+  GW_TRY(cudaEventElapsedTime(&ms_ab, ea0, ea1));
+  ctx->stats.ms_step_c_kernel += ms_ck;
+  ctx->stats.ms_step_ab += ms_ab;
+  long long act = 0, sl_act = 0;
+  double ksum = 0.0;
+  for (size_t t = 0; t < h_counts.size(); ++t) {
+    act += h_counts[t] > 0;
+    sl_act += h_counts[t];
+    ksum += (double)h_kacc[t];
+  }
+  ctx->stats.tiles_total += (long long)npt * nqt;
+  ctx->stats.tiles_active += act;
+  ctx->stats.slabs_total += (long long)npt * nqt * nslab;
+  ctx->stats.slabs_active += sl_act;
+  for (double v : h_fc) fc_host.push_back(v);
+  ctx->stats.flops_issued += issued + 2.0 * tile * tile * ksum * prods;
   return GW_OK;
 }
 
@@ -810,11 +1081,13 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   int rc;
   if ((rc = build_panels(ctx, thr))) return rc;
   const bool f64 = precision == GW_FP64;
-  if (!f64 && (rc = ensure_panel32(ctx))) return rc;
+  const bool tcpath = precision == GW_BF16X3 || precision == GW_BF16X6;
+  if (!f64 && !tcpath && (rc = ensure_panel32(ctx))) return rc;
+  if (tcpath && (rc = ensure_pt(ctx, precision == GW_BF16X6 ? 3 : 2))) return rc;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;
   // device bytes per operand element: FP64, FP32, or FP32 plus bf16 slices
   const size_t esz = f64 ? sizeof(double)
-                         : sizeof(float) + (precision == GW_BF16X6 ? 6 : precision == GW_BF16X3 ? 4 : 0);
+                         : precision == GW_BF16X6 ? 6 : precision == GW_BF16X3 ? 4 : sizeof(float);
   std::vector<Batch> batches = plan_batches(ctx, esz, ctx->batch_bytes);
   ctx->stats.n_batches = (int)batches.size();
 
@@ -829,7 +1102,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   if ((rc = wsT(ctx, "flag_occ", (size_t)n_at * n_at, &flo))) return rc;
   if ((rc = wsT(ctx, "flag_virt", (size_t)n_at * n_at, &flv))) return rc;
   if (!out_on_device && (rc = wsT(ctx, "chi_stage", (size_t)nri * nri, &stage))) return rc;
-  if (!f64) {
+  if (!f64 && !tcpath) {
     if ((rc = wsT(ctx, "g_occ32", (size_t)nao * nao, &go32))) return rc;
     if ((rc = wsT(ctx, "g_virt32", (size_t)nao * nao, &gv32))) return rc;
   }
@@ -840,7 +1113,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
 
   cudaEvent_t ev[8];
   for (auto& e : ev) GW_TRY(cudaEventCreate(&e));
-  double ms_g = 0, ms_ab = 0, ms_c = 0;
+  double ms_g = 0, ms_c = 0;
   for (int j = tau_first; j < tau_first + tau_count; ++j) {
     GW_TRY(cudaEventRecord(ev[0], ctx->stream));
     gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[j], cso, csv, go, gv,
@@ -856,7 +1129,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
       GW_TRY(cudaMemcpyAsync(hfo.data(), flo, hfo.size(), cudaMemcpyDeviceToHost, ctx->stream));
       GW_TRY(cudaMemcpyAsync(hfv.data(), flv, hfv.size(), cudaMemcpyDeviceToHost, ctx->stream));
     }
-    if (!f64) {
+    if (!f64 && !tcpath) {
       gw::launch_cast_f64_f32(go, go32, (long long)nao * nao, ctx->stream);
       gw::launch_cast_f64_f32(gv, gv32, (long long)nao * nao, ctx->stream);
       GW_CHECK_LAUNCH();
@@ -869,6 +1142,8 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
       const Batch& b = batches[bi];
       if (f64)
         rc = chi_one_batch<double>(ctx, b, go, gv, ctx->d_panel64, thr, acc, fc, precision, bi);
+      else if (tcpath)
+        rc = chi_one_batch_tc(ctx, b, go, gv, thr, acc, fc, precision, bi);
       else
         rc = chi_one_batch<float>(ctx, b, go32, gv32, ctx->d_panel32, thr, acc, fc, precision, bi);
       if (rc) return rc;
@@ -914,11 +1189,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   for (auto& e : ev) cudaEventDestroy(e);
   ctx->stats.flops_useful = ctx->stats.flops_a + ctx->stats.flops_b + ctx->stats.flops_c;
   ctx->stats.ms_greens = ms_g;
-  ctx->stats.ms_step_ab = 0.0;
   ctx->stats.ms_step_c = ms_c;
   ctx->stats.ms_total =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  (void)ms_ab;
   return GW_OK;
 }
 

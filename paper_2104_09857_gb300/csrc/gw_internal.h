@@ -40,6 +40,16 @@ struct PanelTask {
   long long seg;  // mode A: K offset of the owner's segment in X
 };
 
+// One panel problem of the tensor-core steps A/B (see k_tc.cu):
+//   Z[r][n] = sum_k Gg[g_row0 + r][k] * PT[p_row0 + n][k],  k < 64 * ksteps
+struct PanelTaskTC {
+  long long panel_off;  // FP64 panel in the pool (transpose build)
+  long long seg;        // mode 0: K offset of the owner's segment in X
+  int g_row0, p_row0, ksteps;
+  int K, N, npw, nsig, p0, aom;
+  int s_local, owner, lam_off;
+};
+
 struct Batch {
   int s0, s1;         // owner atoms [s0, s1)
   int P0, P1;         // RI window of X rows
@@ -93,6 +103,15 @@ struct gw_ctx {
   bool panel32_ok = false;
   int* d_lam = nullptr;
   long long lam_total = 0;
+
+  // transposed, split panels for the tensor-core steps A/B
+  bool pt_ok = false;
+  int pt_slices = 0;
+  double pt_thr = -1.0;
+  void* d_pt = nullptr;           // [slices][pt_rows][pt_kmax] bf16
+  long long pt_rows = 0;
+  int pt_kmax = 0;
+  std::vector<gw::PanelTaskTC> pt_tasks;  // per atom (K == 0: none)
 
   // options
   double batch_bytes = 64e9;

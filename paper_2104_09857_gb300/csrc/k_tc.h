@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "gw_internal.h"
+
 namespace gw {
 
 // 3D TMA map over bf16 slices stored [slices][rows][k_len] (k contiguous);
@@ -20,7 +22,23 @@ int launch_chi_tc(int slices, const CUtensorMap& mx, const CUtensorMap& my, cons
                   int n_tiles, const int* tasks, const int* counts, int max_slab,
                   const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
                   double* chi, int flush_k, int* err_flag, cudaStream_t st);
-// FP32 -> `slices` bf16 slices, out[s * n + i].
-void launch_split_bf16(int slices, const float* x, void* out, long long n, cudaStream_t st);
+// Steps A/B on the tensor cores (PanelJob in k_tc.cu): mode 0 writes X, mode
+// 1 writes Y, as bf16 slices, and accumulates squared atom-block norms.
+int launch_panel_tc(int slices, const CUtensorMap& mg, const CUtensorMap& mp, const int4* tiles,
+                    int n_tiles, const PanelTaskTC* tasks, int mode, int rows_valid, void* out,
+                    long long slice_elems, long long ldk, int P0b, const long long* rowbase,
+                    const int* rowmul, const int* row_slocal, float* norm2, const int* atom_of_ri,
+                    const int* atom_of_ao, int n_at, int npa, int pa0, int flush_k, int* err_flag,
+                    cudaStream_t st);
+void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
+                     int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
+                     long long slice_elems, void* out, cudaStream_t st);
+void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
+                             int kmax, int slices, long long slice_elems, void* out, cudaStream_t st);
+void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
+                                const int* ri_off, const int* ao_off, const int* n_ao, int s0,
+                                int ns, const long long* seg, int pa0, int npa, int n_at,
+                                double thr, int naop, const float* norm2, unsigned char* blockflag,
+                                unsigned char* tileflag, int ntile, int tile_rows, cudaStream_t st);
 
 }  // namespace gw

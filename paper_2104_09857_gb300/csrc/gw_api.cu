@@ -88,6 +88,16 @@ int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
   return GW_OK;
 }
 
+// release every scratch buffer of a context (before a route with different
+// buffer sizes, so that two routes' operands are never resident together)
+void ws_release_all(gw_ctx* ctx) {
+  auto& wb = work_registry()[ctx].m;
+  if (wb.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : wb) cudaFree(kv.second.first);
+  wb.clear();
+}
+
 template <typename T>
 int wsT(gw_ctx* ctx, const char* name, size_t count, T** out) {
   void* p = nullptr;
@@ -545,7 +555,7 @@ int ensure_pt(gw_ctx* ctx, int slices) {
     t.aom = ctx->ao_off[s];
     t.owner = s;
     t.lam_off = d.lam_off;
-    t.ksteps = (d.K + 63) / 64;
+    t.ksteps = (d.K + 63) / 64;  // K steps of 64 (the tensor-core stage width)
     t.p_row0 = (int)rows;
     const int npad = (t.N + 127) / 128 * 128;
     rows += npad;
@@ -628,8 +638,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       t.seg = b.seg[s - b.s0];
       t.s_local = s - b.s0;
       const int ntn = (t.N + tile - 1) / tile;
-      for (int mt = 0; mt < rows_a / tile; ++mt)
-        for (int nt = 0; nt < ntn; ++nt) tiles.push_back(make_int4((int)ta.size(), mt, nt, 0));
+      for (int nt = 0; nt < ntn; ++nt)
+        for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), mt, nt, 0));
       issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
       ta.push_back(t);
     }
@@ -668,8 +678,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (t.K == 0) continue;
       t.g_row0 = (int)tb.size() * rows_b;
       const int ntn = (t.N + tile - 1) / tile;
-      for (int mt = 0; mt < rows_b / tile; ++mt)
-        for (int nt = 0; nt < ntn; ++nt) tiles.push_back(make_int4((int)tb.size(), mt, nt, 0));
+      for (int nt = 0; nt < ntn; ++nt)
+        for (int mt = 0; mt < rows_b / tile; ++mt) tiles.push_back(make_int4((int)tb.size(), mt, nt, 0));
       issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_b / tile) * ntn;
       tb.push_back(t);
     }
@@ -1082,6 +1092,10 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   if ((rc = build_panels(ctx, thr))) return rc;
   const bool f64 = precision == GW_FP64;
   const bool tcpath = precision == GW_BF16X3 || precision == GW_BF16X6;
+  if (ctx->last_precision != precision) {
+    ws_release_all(ctx);
+    ctx->last_precision = precision;
+  }
   if (!f64 && !tcpath && (rc = ensure_panel32(ctx))) return rc;
   if (tcpath && (rc = ensure_pt(ctx, precision == GW_BF16X6 ? 3 : 2))) return rc;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;

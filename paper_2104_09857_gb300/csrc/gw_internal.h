@@ -45,7 +45,7 @@ struct PanelTask {
 struct PanelTaskTC {
   long long panel_off;  // FP64 panel in the pool (transpose build)
   long long seg;        // mode 0: K offset of the owner's segment in X
-  int g_row0, p_row0, ksteps;
+  int g_row0, p_row0, ksteps;  // ksteps: K steps of 64
   int K, N, npw, nsig, p0, aom;
   int s_local, owner, lam_off;
 };
@@ -116,7 +116,8 @@ struct gw_ctx {
   // options
   double batch_bytes = 64e9;
   int batch_atoms = 0;
-  int flush_k = 256;  // tensor-core step C: FP32 accumulator drained every flush_k elements
+  int flush_k = 256;
+  int last_precision = -1;  // tensor-core step C: FP32 accumulator drained every flush_k elements
 
   gw_stats stats{};
 };

@@ -100,8 +100,8 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 128-byte rows,
-// 8-row groups 1024 bytes apart, 1024-aligned tile base.
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 128-byte rows
+// (64 bf16), 8-row groups 1024 bytes apart, 1024-aligned tile base.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
@@ -139,13 +139,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Per-epilogue-warp staging for coalesced stores: 32 rows x 34 bf16, or
+// 32 rows x 17 floats (both 2176 bytes).
+constexpr int kStgBytes = 2176;
+
 template <int S>
 struct Smem {
   static constexpr int kStages = (S == 2) ? 3 : 2;
   static constexpr int kTileBytes = kTileM * kStageK * 2;  // 16 KB, A and B alike
   static constexpr int kStageBytes = 2 * S * kTileBytes;
   static constexpr int kOperandBytes = kStages * kStageBytes;
-  static constexpr int kTotal = kOperandBytes + 256 + 1024;
+  static constexpr int kStagingBytes = kEpiWarps * kStgBytes;
+  static constexpr int kTotal = kOperandBytes + kStagingBytes + 256 + 1024;
 };
 
 // ---------------------------------------------------------------------------
@@ -209,15 +214,25 @@ struct ChiJob {
       return x;
     }
   };
-  // add the register sums of one thread (row r, 64 columns) into chi
-  __device__ void write(float (&acc)[kEpiCols], const Tile& T, int r, int c0) const {
-    const int p = T.ya + r;
-    if (p >= prow) return;
-    double* row = chi + static_cast<long long>(P0 + p) * nri;
+  // Add the register sums of a warp (rows quad*32.., 64 columns from c0) into
+  // chi, 16 columns at a time through the warp's staging buffer so that each
+  // store instruction covers two rows of 16 consecutive doubles.
+  __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
+                        uint8_t* stg) const {
+    float* f = reinterpret_cast<float*>(stg);  // [32][17]
 #pragma unroll
-    for (int j = 0; j < kEpiCols; ++j) {
-      const int q = T.yb + c0 + j;
-      if (q < nri) row[q] -= static_cast<double>(acc[j]);
+    for (int cc = 0; cc < kEpiCols; cc += 16) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) f[lane * 17 + j] = acc[cc + j];
+      __syncwarp();
+      const int col = lane & 15, sub = lane >> 4;
+      const int q = T.yb + c0 + cc + col;
+#pragma unroll
+      for (int i = 0; i < 32; i += 2) {
+        const int p = T.ya + quad * 32 + i + sub;
+        if (p < prow && q < nri) chi[static_cast<long long>(P0 + p) * nri + q] -= static_cast<double>(f[(i + sub) * 17 + col]);
+      }
+      __syncwarp();
     }
   }
 };
@@ -268,56 +283,105 @@ struct PanelJob {
       return v;
     }
   };
-  __device__ void write(float (&acc)[kEpiCols], const Tile& T, int r_local, int c0) const {
+  __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
+                        uint8_t* stg) const {
     const PanelTaskTC& tk = tasks[T.task];
-    const int r = T.mt * kTileM + r_local;
-    if (r >= rows_valid) return;
-    long long rb;
-    int rm, s_local, m_row;
-    if (mode == 0) {
-      rb = tk.seg + static_cast<long long>(r) * tk.nsig;
-      rm = 0;
-      s_local = tk.s_local;
-      m_row = atom_of_ao[r];
-    } else {
-      rb = rowbase[r];
-      rm = rowmul[r];
-      s_local = row_slocal[r];
-      m_row = tk.owner;
+    const int r = T.mt * kTileM + quad * 32 + lane;
+    const bool row_ok = r < rows_valid;
+    long long rb = 0;
+    int rm = 0, s_local = 0, m_row = 0;
+    if (row_ok) {
+      if (mode == 0) {
+        rb = tk.seg + static_cast<long long>(r) * tk.nsig;
+        s_local = tk.s_local;
+        m_row = atom_of_ao[r];
+      } else {
+        rb = rowbase[r];
+        rm = rowmul[r];
+        s_local = row_slocal[r];
+        m_row = tk.owner;
+      }
     }
+    // Walk this row's columns n = nbase + j in 16-column groups parked in the
+    // thread's own staging row (no cross-lane traffic, so no warp sync): the
+    // squared block norms for both modes, and the Y stores of mode 1 (there
+    // consecutive rows sigma are consecutive in memory).
+    float* f = reinterpret_cast<float*>(stg) + lane * 17;
+    const int nbase = T.nt * kTileN + c0;
+    int pw = nbase / tk.nsig;
+    int sp = nbase - pw * tk.nsig;
     int key = -1;
     float ss = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < kEpiCols; ++j) {
-      const int n = T.nt * kTileN + c0 + j;
-      if (n >= tk.N) break;
-      const int pw = n / tk.nsig;
-      const int sp = n - pw * tk.nsig;
-      const int P = tk.p0 + pw;
-      long long dst;
-      int blk;
-      const int patom = atom_of_ri[P];
-      if (mode == 0) {
-        dst = static_cast<long long>(P - P0b) * ldk + rb + sp;
-        blk = (s_local * n_at + m_row) * npa + (patom - pa0);
-      } else {
-        dst = static_cast<long long>(P) * ldk + rb + static_cast<long long>(tk.aom + sp) * rm;
-        blk = (s_local * n_at + m_row) * n_at + patom;
-      }
-      float v = acc[j];
-      if (blk != key) {
-        if (key >= 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
-        key = blk;
-        ss = 0.f;
-      }
-      ss += v * v;
-      for (int s = 0; s < slices; ++s) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        out[s * slice_elems + dst] = h;
-        v -= __bfloat162float(h);
+    int patom = -1, patom_pw = -1;
+#pragma unroll
+    for (int cc = 0; cc < kEpiCols; cc += 16) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) f[j] = acc[cc + j];
+      if (row_ok) {
+        for (int j = 0; j < 16; ++j) {
+          const int n = nbase + cc + j;
+          if (n >= tk.N) break;
+          if (pw != patom_pw) {
+            patom = atom_of_ri[tk.p0 + pw];
+            patom_pw = pw;
+          }
+          const int blk = mode == 0 ? (s_local * n_at + m_row) * npa + (patom - pa0)
+                                    : (s_local * n_at + m_row) * n_at + patom;
+          float v = f[j];
+          if (blk != key) {
+            if (key >= 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
+            key = blk;
+            ss = 0.f;
+          }
+          ss += v * v;
+          if (mode == 1) {
+            const long long dst = static_cast<long long>(tk.p0 + pw) * ldk + rb +
+                                  static_cast<long long>(tk.aom + sp) * rm;
+            for (int s = 0; s < slices; ++s) {
+              const __nv_bfloat16 h = __float2bfloat16_rn(v);
+              out[s * slice_elems + dst] = h;
+              v -= __bfloat162float(h);
+            }
+          }
+          if (++sp == tk.nsig) {
+            sp = 0;
+            ++pw;
+          }
+        }
       }
     }
     if (key >= 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
+    if (mode == 1) return;
+    // X: consecutive columns (s' of one RI function) are consecutive in
+    // memory; stage each slice through smem and store column-wise.
+    __syncwarp();
+    __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(stg);  // [32][34]
+    const int mu0 = T.mt * kTileM + quad * 32;
+#pragma unroll
+    for (int cc = 0; cc < kEpiCols; cc += 32) {
+      const int n = nbase + cc + lane;
+      const bool n_ok = n < tk.N;
+      const int cpw = n_ok ? n / tk.nsig : 0;
+      const int csp = n - cpw * tk.nsig;
+      const long long colbase = static_cast<long long>(tk.p0 + cpw - P0b) * ldk + tk.seg + csp;
+      for (int s = 0; s < slices; ++s) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const __nv_bfloat16 b = __float2bfloat16_rn(acc[cc + j]);
+          h[lane * 34 + j] = b;
+          acc[cc + j] -= __bfloat162float(b);
+        }
+        __syncwarp();
+        if (n_ok) {
+          for (int i = 0; i < 32; ++i) {
+            const int mu = mu0 + i;
+            if (mu < rows_valid)
+              out[s * slice_elems + colbase + static_cast<long long>(mu) * tk.nsig] = h[i * 34 + lane];
+          }
+        }
+        __syncwarp();
+      }
+    }
   }
 };
 
@@ -335,7 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* operands = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOperandBytes);
+  uint8_t* staging = smem + L::kOperandBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOperandBytes + L::kStagingBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* acc_full = bars + 2 * kStages;
@@ -488,8 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..9) ----------------
     const int quad = warp & 3;
     const int half = (warp - 2) >> 2;
-    const int r_local = quad * 32 + lane;
     const int c0 = half * kEpiCols;
+    uint8_t* stg = staging + (warp - 2) * kStgBytes;
     const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16);
     float acc[kEpiCols];
     int chunk = 0;
@@ -521,13 +586,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[buf]);
         if (Job::kPeriodic && (c + 1) % kFlushChunks == 0 && c + 1 < nch) {
-          job.write(acc, T, r_local, c0);
+          job.write(acc, T, quad, lane, c0, stg);
 #pragma unroll
           for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
         }
       }
       if (!ok) break;
-      if (nch > 0) job.write(acc, T, r_local, c0);
+      if (nch > 0) job.write(acc, T, quad, lane, c0, stg);
     }
     if (!ok) {
       *abort_flag = 1;

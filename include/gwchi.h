@@ -118,6 +118,24 @@ int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
 int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
                int screening, double* chi_out, int out_on_device);
 
+/* Screening chain from chi(i tau) to the correlation part of the screened
+ * interaction W^c(i tau), all in FP64 on the device:
+ *   chi(i omega_k) = sum_j gamma[k][j] chi(i tau_j)        (cosine transform)
+ *   eps_k = 1 - L^T chi(i omega_k) L,  V = L L^T              (Eq. 7, Eq. 8)
+ *   W^c(i omega_k) = L (eps_k^-1 - 1) L^T, eps_k inverted through its
+ *   Cholesky factor eps_k = R R^T as Z^T Z - V, Z = R^-1 L^T  (Eq. 9)
+ *   W^c(i tau_j) = sum_k delta[j][k] W^c(i omega_k)           (back transform)
+ * The RI overlap metric is taken as the identity (Eqs. 5-6 reduce to chi).
+ * V[n_ri*n_ri]: host, symmetric positive definite (GW_ERR_NOT_SPD otherwise);
+ * gamma[n_omega][n_tau], delta[n_tau][n_omega]: host transform weights;
+ * chi_tau[n_tau][n_ri][n_ri] (device if chi_on_device, else host), as returned
+ * by gw_chi_tau; w_tau_out[n_tau][n_ri][n_ri] (device if out_on_device).
+ * GW_ERR_NOT_SPD also when some eps_k is not positive definite (chi must be
+ * negative semidefinite).  Requires gw_set_basis and gw_set_greens (tau grid). */
+int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const double* gamma,
+                const double* delta, const double* chi_tau, int chi_on_device,
+                double* w_tau_out, int out_on_device);
+
 /* chi_PQ(i tau) for one tau point in FP64 without allocating device memory.
  * The paper has no counterpart: this is a service for callers that cannot
  * call cudaMalloc when they need chi -- a host framework whose caching

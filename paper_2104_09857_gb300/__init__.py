@@ -94,6 +94,27 @@ class Context:
                             out.data_ptr(), True)
         return out
 
+    def chi_to_w(self, chi, V, gamma, delta, out=None):
+        """W^c(i tau) from chi(i tau) through the FP64 screening chain (Eqs. 7-9
+        with cosine transforms).  `chi`: device tensor or host array
+        [n_tau, n_RI, n_RI]; returns a device tensor unless `out` is a host array."""
+        torch = self._torch
+        n_tau = len(gamma[0]) if np.ndim(gamma) == 2 else 0
+        shape = (n_tau, self.nri, self.nri)
+        if isinstance(chi, np.ndarray):
+            chi = np.ascontiguousarray(chi, dtype=np.float64)
+            chi_ptr, chi_dev = chi.ctypes.data, False
+        else:
+            assert chi.dtype == torch.float64 and chi.is_contiguous()
+            chi_ptr, chi_dev = chi.data_ptr(), True
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device=f"cuda:{self.device}")
+        if isinstance(out, np.ndarray):
+            _lib.gw_chi_to_w(self.ctx, V, gamma, delta, chi_ptr, chi_dev, out.ctypes.data, False)
+        else:
+            _lib.gw_chi_to_w(self.ctx, V, gamma, delta, chi_ptr, chi_dev, out.data_ptr(), True)
+        return out
+
     def stats(self) -> dict:
         return _lib.gw_get_stats(self.ctx)
 

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("gw_get_stats", _I, [_P, ctypes.POINTER(gw_stats)]),
     ("gw_set_option", _I, [_P, ctypes.c_char_p, _D]),
     ("gw_chi_tau_noalloc", _I, [_P, _I, _D, _P]),
+    ("gw_chi_to_w", _I, [_P, _P, _I, _P, _P, _P, _I, _P, _I]),
 ]
 
 
@@ -167,6 +168,15 @@ def gw_chi_tau_noalloc(ctx: int, tau_index: int, thr: float, out_ptr: int) -> No
     """FP64 chi for one tau point into a device buffer, with no device
     allocation inside the library (fixed work array; see include/gwchi.h)."""
     _check(ctx, lib().gw_chi_tau_noalloc(ctx, int(tau_index), float(thr), out_ptr))
+
+
+def gw_chi_to_w(ctx: int, V, gamma, delta, chi_ptr: int, chi_on_device: bool, out_ptr: int,
+                out_on_device: bool) -> None:
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    _check(ctx, lib().gw_chi_to_w(ctx, _ptr(V), gamma.shape[0], _ptr(gamma), _ptr(delta), chi_ptr,
+                                  int(bool(chi_on_device)), out_ptr, int(bool(out_on_device))))
 
 
 def gw_get_stats(ctx: int) -> dict:

@@ -1,0 +1,78 @@
+"""Parity of the FP64 screening chain on the GPU (gw_chi_to_w) with the CPU
+oracle: chi -> chi(i omega) -> eps -> W^c(i omega) -> W^c(i tau)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import chain as och  # noqa: E402
+from oracle import chi as oc  # noqa: E402
+from synth import make_case  # noqa: E402
+from synth.chain_inputs import chain_inputs  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_09857_gb300 as p
+
+    return p
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", ["benzene", "ribbon28"])
+def test_chain_matches_oracle_on_oracle_chi(pkg, name):
+    """Same chi in, W^c(i tau) out: GPU chain vs oracle chain."""
+    case = make_case(name, n_tau=8)
+    chi = oc.chi_dense(case)
+    omega, gamma, delta, v, _, _ = chain_inputs(case)
+    ref, _ = och.chi_to_w(chi, v, gamma, delta)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        got = ctx.chi_to_w(chi, v, gamma, delta).cpu().numpy()
+    for j in range(len(case.tau)):
+        assert _rel(got[j], ref[j]) <= TOL, f"tau {j}: {_rel(got[j], ref[j]):.3e}"
+
+
+def test_chain_from_gpu_chi_host_output(pkg):
+    """chi computed on the device feeds the chain directly; host output."""
+    case = make_case("benzene")
+    omega, gamma, delta, v, _, _ = chain_inputs(case)
+    ref, _ = och.chi_to_w(oc.chi_dense(case), v, gamma, delta)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        chi = ctx.chi_tau(case.thr, "fp64")
+        out = np.zeros(ref.shape)
+        ctx.chi_to_w(chi, v, gamma, delta, out=out)
+    for j in range(len(case.tau)):
+        assert _rel(out[j], ref[j]) <= TOL
+        assert np.abs(out[j] - out[j].T).max() <= 1e-10 * np.abs(out[j]).max()
+
+
+def test_chain_rejects_non_spd(pkg):
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("chain_CH")
+    chi = oc.chi_dense(case)
+    omega, gamma, delta, v, _, _ = chain_inputs(case)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_to_w(chi, -v, gamma, delta)
+        assert e.value.code == -8
+        # a positive chi makes eps indefinite for a large enough scale
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_to_w(-1e6 * chi, v, gamma, delta)
+        assert e.value.code == -8

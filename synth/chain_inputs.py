@@ -63,6 +63,17 @@ def coulomb_matrix(system) -> np.ndarray:
     return v
 
 
+def synthetic_w(nri: int, tau: np.ndarray, seed: int) -> np.ndarray:
+    """Seeded negative semidefinite W(tau_j) = -(R^T R / n_RI) exp(-0.1 tau_j),
+    R [n_RI, n_RI] with N(0,1) entries: a stand-in screened interaction for
+    self-energy tests that do not run the chain."""
+    from .rng import normal_stream
+
+    r = normal_stream(seed, 13, 0, nri * nri).reshape(nri, nri)
+    w0 = -(r.T @ r) / nri
+    return np.stack([w0 * np.exp(-0.1 * t) for t in tau])
+
+
 def chain_inputs(case):
     """omega, gamma, delta and V for a synth Case."""
     eps = case.eps

@@ -1,0 +1,59 @@
+"""Pins of the self-energy oracle (Eq. 10): the AO route against the MO
+route, the W = 1 special case, the sign for negative semidefinite W, and
+linearity in W.  No GPU."""
+
+import numpy as np
+import pytest
+
+from oracle import chi as oc
+from oracle import sigma as osg
+from synth import make_case
+from synth.chain_inputs import synthetic_w
+
+
+@pytest.fixture(scope="module")
+def setup():
+    case = make_case("chain_CHCH", n_tau=3)
+    s = case.system
+    t = oc.dense_three_center(s.n_ao, s.n_ri, case.t3c.blocks, case.t3c.offsets, case.t3c.data)
+    w = synthetic_w(s.nri_total, case.tau, 5)
+    orbs = [case.n_occ - 1, case.n_occ]
+    return case, t, w, orbs
+
+
+def test_ao_route_equals_mo_route(setup):
+    case, t, w, orbs = setup
+    got = osg.sigma_dense(case, w, orbs, thr=0.0)
+    for a, n in enumerate(orbs):
+        for j, tau in enumerate(case.tau):
+            ref = osg.sigma_mo(t, case.C, case.eps, case.n_occ, case.mu_fermi, n, w[j], tau)
+            assert got[a, j, 0] == pytest.approx(ref[0], rel=1e-11)
+            assert got[a, j, 1] == pytest.approx(ref[1], rel=1e-11)
+
+
+def test_identity_w_is_trace_of_g_b_bt(setup):
+    case, t, _, orbs = setup
+    n = orbs[0]
+    b = osg.b_half(t, case.C, n)
+    go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, 0.4)
+    eye = np.eye(b.shape[1])
+    # sum_{mu nu} G_{mu nu} sum_P B_{mu P} B_{nu P}, by loops over P
+    ref = sum(float(b[:, p] @ go @ b[:, p]) for p in range(b.shape[1]))
+    assert osg.s_term(go, b, eye) == pytest.approx(ref, rel=1e-12)
+
+
+def test_sign_and_linearity(setup):
+    """W <= 0 and G >= 0 give S <= 0, so Sigma(i tau) >= 0 and Sigma(-i tau) <= 0;
+    Sigma is linear in W."""
+    case, _, w, orbs = setup
+    sg = osg.sigma_dense(case, w, orbs, thr=0.0)
+    assert np.all(sg[:, :, 0] >= 0.0) and np.all(sg[:, :, 1] <= 0.0)
+    sg2 = osg.sigma_dense(case, 2.5 * w, orbs, thr=0.0)
+    assert np.allclose(sg2, 2.5 * sg, rtol=1e-12)
+
+
+def test_filter_threshold_zero_and_tiny_agree(setup):
+    case, _, w, orbs = setup
+    a = osg.sigma_dense(case, w, orbs, thr=0.0)
+    b = osg.sigma_dense(case, w, orbs, thr=1e-300)
+    assert np.array_equal(a, b)

@@ -118,6 +118,19 @@ int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
 int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
                int screening, double* chi_out, int out_on_device);
 
+/* Diagonal correlation self-energy of Eq. 10 for the orbitals listed:
+ *   B^n[mu][P] = sum_nu C[nu][n] (nu mu | P)  (half transform of the 3c tensor)
+ *   S^g_n(tau) = sum_{mu nu} G^g_{mu nu}(tau) sum_{PQ} B^n_{mu P} W_PQ(tau) B^n_{nu Q}
+ *   sigma_out[a][j][0] = Sigma^c_n(i tau_j)  = -S^occ_n(tau_j)
+ *   sigma_out[a][j][1] = Sigma^c_n(-i tau_j) = +S^virt_n(tau_j),  n = orbitals[a]
+ * (real, phases removed as for chi; W even in tau; RI metric = identity).
+ * W_tau[n_tau][n_ri][n_ri]: device if w_on_device else host (e.g. the output
+ * of gw_chi_to_w).  Filter: 3c, G and (mu-atom, P-atom) blocks of B^n with
+ * norm < thr are dropped.  precision: GW_FP64 only.  sigma_out: host,
+ * [n_orb][n_tau][2].  Uses the tensor, orbitals and tau grid of the context. */
+int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
+                 int n_orb, double thr, int precision, double* sigma_out);
+
 /* Screening chain from chi(i tau) to the correlation part of the screened
  * interaction W^c(i tau), all in FP64 on the device:
  *   chi(i omega_k) = sum_j gamma[k][j] chi(i tau_j)        (cosine transform)

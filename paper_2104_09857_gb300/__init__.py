@@ -115,6 +115,16 @@ class Context:
             _lib.gw_chi_to_w(self.ctx, V, gamma, delta, chi_ptr, chi_dev, out.data_ptr(), True)
         return out
 
+    def sigma_tau(self, w_tau, orbitals, thr: float, precision: str = "fp64"):
+        """Diagonal Sigma^c_n(+-i tau) (Eq. 10): numpy [n_orb, n_tau, 2]."""
+        torch = self._torch
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if isinstance(w_tau, np.ndarray):
+            w = np.ascontiguousarray(w_tau, dtype=np.float64)
+            return _lib.gw_sigma_tau(self.ctx, w.ctypes.data, False, orbitals, self.n_tau, thr, prec)
+        assert w_tau.dtype == torch.float64 and w_tau.is_contiguous()
+        return _lib.gw_sigma_tau(self.ctx, w_tau.data_ptr(), True, orbitals, self.n_tau, thr, prec)
+
     def stats(self) -> dict:
         return _lib.gw_get_stats(self.ctx)
 

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("gw_set_option", _I, [_P, ctypes.c_char_p, _D]),
     ("gw_chi_tau_noalloc", _I, [_P, _I, _D, _P]),
     ("gw_chi_to_w", _I, [_P, _P, _I, _P, _P, _P, _I, _P, _I]),
+    ("gw_sigma_tau", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
 ]
 
 
@@ -177,6 +178,16 @@ def gw_chi_to_w(ctx: int, V, gamma, delta, chi_ptr: int, chi_on_device: bool, ou
     delta = np.ascontiguousarray(delta, dtype=np.float64)
     _check(ctx, lib().gw_chi_to_w(ctx, _ptr(V), gamma.shape[0], _ptr(gamma), _ptr(delta), chi_ptr,
                                   int(bool(chi_on_device)), out_ptr, int(bool(out_on_device))))
+
+
+def gw_sigma_tau(ctx: int, w_ptr: int, w_on_device: bool, orbitals, n_tau: int, thr: float,
+                 precision: int = GW_FP64) -> np.ndarray:
+    """[n_orb, n_tau, 2]: (Sigma^c_n(i tau), Sigma^c_n(-i tau)) for the orbitals."""
+    orbitals = np.ascontiguousarray(orbitals, dtype=np.int32)
+    out = np.zeros((orbitals.size, n_tau, 2))
+    _check(ctx, lib().gw_sigma_tau(ctx, w_ptr, int(bool(w_on_device)), _ptr(orbitals), orbitals.size,
+                                   float(thr), int(precision), _ptr(out)))
+    return out
 
 
 def gw_get_stats(ctx: int) -> dict:

@@ -831,6 +831,10 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
 
 }  // namespace
 
+namespace gw {
+int build_panels_for(gw_ctx* ctx, double thr) { return build_panels(ctx, thr); }
+}  // namespace gw
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

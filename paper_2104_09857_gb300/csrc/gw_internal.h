@@ -58,6 +58,10 @@ struct Batch {
   std::vector<long long> seg;  // per owner: K offset
 };
 
+// Builds (or reuses) the owner panels of the 3c tensor for filter threshold
+// thr; defined with the chi orchestration.
+int build_panels_for(gw_ctx* ctx, double thr);
+
 }  // namespace gw
 
 struct gw_ctx {

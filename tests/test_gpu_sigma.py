@@ -1,0 +1,61 @@
+"""Parity of the diagonal self-energy (Eq. 10, gw_sigma_tau, FP64) with the
+CPU oracle, and the whole chain chi -> W -> Sigma on one small system."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import chain as och  # noqa: E402
+from oracle import chi as oc  # noqa: E402
+from oracle import sigma as osg  # noqa: E402
+from synth import make_case  # noqa: E402
+from synth.chain_inputs import chain_inputs, synthetic_w  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_09857_gb300 as p
+
+    return p
+
+
+@pytest.mark.parametrize("name,thr", [("chain_CHCH", 0.0), ("benzene", 0.0), ("ribbon28", 1e-9),
+                                      ("ribbon28", 1e-3)])
+def test_sigma_matches_oracle_synthetic_w(pkg, name, thr):
+    case = make_case(name, n_tau=4)
+    w = synthetic_w(case.system.nri_total, case.tau, 5)
+    orbs = [case.n_occ - 1, case.n_occ, 0]
+    ref = osg.sigma_dense(case, w, orbs, thr=thr)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        got = ctx.sigma_tau(w, orbs, thr)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= TOL * scale
+    assert np.all(got[:, :, 0] >= -TOL * scale) and np.all(got[:, :, 1] <= TOL * scale)
+
+
+def test_chi_w_sigma_chain_on_device(pkg):
+    """chi (GPU) -> W^c (GPU chain) -> Sigma (GPU), all on the device, against
+    the same composition of oracles."""
+    case = make_case("benzene")
+    omega, gamma, delta, v, _, _ = chain_inputs(case)
+    orbs = [case.n_occ - 1, case.n_occ]
+    chi_ref = oc.chi_dense(case)
+    w_ref, _ = och.chi_to_w(chi_ref, v, gamma, delta)
+    s_ref = osg.sigma_dense(case, w_ref, orbs)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        chi = ctx.chi_tau(case.thr, "fp64")
+        w = ctx.chi_to_w(chi, v, gamma, delta)
+        got = ctx.sigma_tau(w, orbs, case.thr)
+    assert np.abs(got - s_ref).max() <= 1e-9 * np.abs(s_ref).max()

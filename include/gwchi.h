@@ -71,6 +71,8 @@ typedef struct gw_stats {
   long long kernel_launches; /* all kernel launches of the last call           */
   double bytes_operands; /* bytes of X and Y operands written by steps A/B      */
   int n_batches;
+  long long tasks_seen;    /* learned screening: step-C tasks examined            */
+  long long tasks_skipped; /* learned screening: tasks dropped by the prediction  */
 } gw_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -171,6 +173,43 @@ int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const double* gamma,
  * context's device.  Runs on the context's stream and returns after it has
  * drained.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double* chi_out_device);
+
+/* Learned screening of step-C tasks.  Not in the paper: an addition of the
+ * hot-path specification.  A task is one (128 x 128 chi tile, 64-function K
+ * slab) pair of the tensor-core route that survives the exact block filter;
+ * its 8 features are log10 of the norm bounds of its X and Y parts (from the
+ * accumulated atom-block norms), log10 tau, three centroid distances (sigma
+ * atom to row tile, AO chunk to column tile, row tile to column tile, in
+ * units of 10 A), the sigma atom's basis size / 13, and the log10 norm-product
+ * bound.  The network (8 -> 64 -> 64 -> 1, ReLU, bf16 weights, FP32
+ * accumulation) plus the log bound feature (a skip connection: it learns
+ * log10 of actual norm / bound) predicts log10 of the task's contribution
+ * norm; with
+ * screening = GW_SCREEN_MLP, gw_chi_tau drops a task when
+ * prediction + margin < log10(thr) (option "mlp_margin", default 0.5).
+ *
+ * gw_mlp_log: run gw_chi_tau on the tensor-core route and record every task's
+ *   features [n][8] and the log10 Frobenius norm of its actual contribution
+ *   (computed from the same operands); up to cap rows are copied out, n_out =
+ *   rows logged.
+ * gw_mlp_init: seeded He-normal weights, zero biases.
+ * gw_mlp_set_params / gw_mlp_get_params: flat FP32 master weights, layout
+ *   W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3[1] (n = 4801).
+ * gw_mlp_grad: mean-squared-error loss and its gradient w.r.t. the bf16
+ *   weights on the given samples (forward and backward kernels).
+ * gw_mlp_train: Adam (lr) on mini-batches of a shuffled copy for `epochs`;
+ *   loss_per_epoch[e] (may be NULL) = training loss after epoch e.
+ * gw_mlp_predict: forward pass. */
+int gw_mlp_log(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
+               float* feat_out, float* target_out, long long cap, long long* n_out);
+int gw_mlp_init(gw_ctx* ctx, unsigned long long seed);
+int gw_mlp_set_params(gw_ctx* ctx, const float* theta, long long n);
+int gw_mlp_get_params(gw_ctx* ctx, float* theta, long long n);
+int gw_mlp_grad(gw_ctx* ctx, const float* feat, const float* target, long long n, float* loss,
+                float* grad);
+int gw_mlp_train(gw_ctx* ctx, const float* feat, const float* target, long long n, int epochs,
+                 long long batch, float lr, unsigned long long seed, float* loss_per_epoch);
+int gw_mlp_predict(gw_ctx* ctx, const float* feat, long long n, float* pred);
 
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);

@@ -9,7 +9,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Parameters, in the flat order shared with the library:
     W1 [H][F], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1]
 Forward:   z1 = W1 x + b1, h1 = relu(z1), z2 = W2 h1 + b2, h2 = relu(z2),
-           y = w3 . h2 + b3
+           y = w3 . h2 + b3 + x[BOUND]
+(the last feature is log10 of the norm-product bound of a task; the network
+learns the residual, log10 of actual norm / bound, which is <= 0)
 Loss:      L = mean_s (y_s - t_s)^2
 Gradients are taken with respect to the bf16-rounded weights and applied to
 the master weights (straight-through rounding).
@@ -20,6 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 64
+BOUND = 7  # index of the log10 norm-product bound among the features
 
 
 def n_params(n_feat: int, hidden: int = HIDDEN) -> int:
@@ -53,7 +56,7 @@ def forward(theta: np.ndarray, x: np.ndarray, hidden: int = HIDDEN, round_bf16: 
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ w2.T + b2
     h2 = np.maximum(z2, 0.0)
-    y = h2 @ w3 + b3[0]
+    y = h2 @ w3 + b3[0] + x[:, BOUND]
     return y, (z1, h1, z2, h2, th)
 
 

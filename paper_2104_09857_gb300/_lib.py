@@ -61,6 +61,8 @@ class gw_stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong),
         ("bytes_operands", ctypes.c_double),
         ("n_batches", ctypes.c_int),
+        ("tasks_seen", ctypes.c_longlong),
+        ("tasks_skipped", ctypes.c_longlong),
     ]
 
     def as_dict(self) -> dict:
@@ -86,7 +88,17 @@ SIGNATURES = [
     ("gw_chi_tau_noalloc", _I, [_P, _I, _D, _P]),
     ("gw_chi_to_w", _I, [_P, _P, _I, _P, _P, _P, _I, _P, _I]),
     ("gw_sigma_tau", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
+    ("gw_mlp_log", _I, [_P, _I, _I, _D, _I, _P, _P, _LL, ctypes.POINTER(_LL)]),
+    ("gw_mlp_init", _I, [_P, ctypes.c_ulonglong]),
+    ("gw_mlp_set_params", _I, [_P, _P, _LL]),
+    ("gw_mlp_get_params", _I, [_P, _P, _LL]),
+    ("gw_mlp_grad", _I, [_P, _P, _P, _LL, _P, _P]),
+    ("gw_mlp_train", _I, [_P, _P, _P, _LL, _I, _LL, ctypes.c_float, ctypes.c_ulonglong, _P]),
+    ("gw_mlp_predict", _I, [_P, _P, _LL, _P]),
 ]
+
+MLP_FEATURES = 8
+MLP_PARAMS = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -188,6 +200,58 @@ def gw_sigma_tau(ctx: int, w_ptr: int, w_on_device: bool, orbitals, n_tau: int, 
     _check(ctx, lib().gw_sigma_tau(ctx, w_ptr, int(bool(w_on_device)), _ptr(orbitals), orbitals.size,
                                    float(thr), int(precision), _ptr(out)))
     return out
+
+
+def gw_mlp_log(ctx: int, tau_first: int, tau_count: int, thr: float, precision: int,
+               cap: int = 1 << 22):
+    """(features [n, 8], log10 contribution norms [n]) of every step-C task."""
+    feat = np.zeros((cap, MLP_FEATURES), dtype=np.float32)
+    tgt = np.zeros(cap, dtype=np.float32)
+    n = _LL(0)
+    _check(ctx, lib().gw_mlp_log(ctx, tau_first, tau_count, float(thr), int(precision), _ptr(feat),
+                                 _ptr(tgt), cap, ctypes.byref(n)))
+    m = min(n.value, cap)
+    return feat[:m].copy(), tgt[:m].copy()
+
+
+def gw_mlp_init(ctx: int, seed: int) -> None:
+    _check(ctx, lib().gw_mlp_init(ctx, int(seed)))
+
+
+def gw_mlp_set_params(ctx: int, theta) -> None:
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(ctx, lib().gw_mlp_set_params(ctx, _ptr(theta), theta.size))
+
+
+def gw_mlp_get_params(ctx: int) -> np.ndarray:
+    theta = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(ctx, lib().gw_mlp_get_params(ctx, _ptr(theta), theta.size))
+    return theta
+
+
+def gw_mlp_grad(ctx: int, feat, tgt):
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(ctx, lib().gw_mlp_grad(ctx, _ptr(feat), _ptr(tgt), tgt.size, _ptr(loss), _ptr(grad)))
+    return float(loss[0]), grad
+
+
+def gw_mlp_train(ctx: int, feat, tgt, epochs: int, batch: int, lr: float, seed: int) -> np.ndarray:
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(ctx, lib().gw_mlp_train(ctx, _ptr(feat), _ptr(tgt), tgt.size, int(epochs), int(batch),
+                                   float(lr), int(seed), _ptr(losses)))
+    return losses[:epochs]
+
+
+def gw_mlp_predict(ctx: int, feat) -> np.ndarray:
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    pred = np.zeros(feat.shape[0], dtype=np.float32)
+    _check(ctx, lib().gw_mlp_predict(ctx, _ptr(feat), feat.shape[0], _ptr(pred)))
+    return pred
 
 
 def gw_get_stats(ctx: int) -> dict:

@@ -22,6 +22,7 @@
 #include "gw_internal.h"
 #include "k_simt.h"
 #include "k_tc.h"
+#include "k_mlp.h"
 
 using gw::Batch;
 using gw::kSlabAO;
@@ -430,10 +431,10 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   unsigned char *bx, *by, *fx, *fy;
   if ((rc = wsT(ctx, "bx", (size_t)ns * ctx->n_at * npa, &bx))) return rc;
   if ((rc = wsT(ctx, "by", (size_t)ns * ctx->n_at * ctx->n_at, &by))) return rc;
-  if ((rc = wsT(ctx, "fx", (size_t)nslab * npt, &fx))) return rc;
-  if ((rc = wsT(ctx, "fy", (size_t)nslab * nqt, &fy))) return rc;
-  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)nslab * npt, ctx->stream));
-  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)nslab * nqt, ctx->stream));
+  if ((rc = wsT(ctx, "fx", (size_t)ns * ctx->n_at * npt, &fx))) return rc;
+  if ((rc = wsT(ctx, "fy", (size_t)ns * ctx->n_at * nqt, &fy))) return rc;
+  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)ns * ctx->n_at * npt, ctx->stream));
+  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)ns * ctx->n_at * nqt, ctx->stream));
   long long* d_seg;
   if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
   int* d_nao;
@@ -466,7 +467,8 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
   if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
   gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, ctx->nri, ctx->d_atom_of_ri, d_len,
-                         tasks, counts, kacc, tile, ctx->stream);
+                         tasks, counts, kacc, tile, per, ctx->n_at, ctx->nao, ctx->d_atom_of_ao,
+                         ctx->stream);
   GW_CHECK_LAUNCH();
   double* d_fc;
   if ((rc = wsT(ctx, "fc", (size_t)ns * ctx->n_at, &d_fc))) return rc;
@@ -728,10 +730,10 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   unsigned char *bx, *by, *fx, *fy;
   if ((rc = wsT(ctx, "bx", (size_t)ns * n_at * npa, &bx))) return rc;
   if ((rc = wsT(ctx, "by", (size_t)ns * n_at * n_at, &by))) return rc;
-  if ((rc = wsT(ctx, "fx", (size_t)nslab * npt, &fx))) return rc;
-  if ((rc = wsT(ctx, "fy", (size_t)nslab * nqt, &fy))) return rc;
-  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)nslab * npt, ctx->stream));
-  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)nslab * nqt, ctx->stream));
+  if ((rc = wsT(ctx, "fx", (size_t)ns * ctx->n_at * npt, &fx))) return rc;
+  if ((rc = wsT(ctx, "fy", (size_t)ns * ctx->n_at * nqt, &fy))) return rc;
+  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)ns * ctx->n_at * npt, ctx->stream));
+  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)ns * ctx->n_at * nqt, ctx->stream));
   long long* d_seg;
   int* d_nao;
   if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
@@ -762,7 +764,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
   if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
   gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
-                         counts, kacc, tile, ctx->stream);
+                         counts, kacc, tile, per, n_at, nao, ctx->d_atom_of_ao, ctx->stream);
   double* d_fc;
   int* d_nri;
   if ((rc = wsT(ctx, "fc", (size_t)ns * n_at, &d_fc))) return rc;
@@ -770,6 +772,43 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   gw::launch_count_c(bx, by, ns, n_at, pa0, npa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
   GW_CHECK_LAUNCH();
   ctx->stats.kernel_launches += 4;
+  double fc_scale = 1.0;
+  if (ctx->mlp_mode) {
+    gw::MlpBatch mb{};
+    mb.s0 = b.s0;
+    mb.ns = ns;
+    mb.P0 = b.P0;
+    mb.prow = prow;
+    mb.nslab = nslab;
+    mb.npt = npt;
+    mb.nqt = nqt;
+    mb.tile = tile;
+    mb.per = per;
+    mb.pa0 = pa0;
+    mb.npa = npa;
+    mb.slices = slices;
+    mb.Kb = Kb;
+    mb.xs = xs;
+    mb.ys = ys;
+    mb.bx2 = bx2;
+    mb.by2 = by2;
+    mb.bx = bx;
+    mb.by = by;
+    mb.tasks = tasks;
+    mb.counts = counts;
+    mb.kacc = kacc;
+    mb.slab_k0 = d_k0;
+    mb.slab_len = d_len;
+    mb.tau = ctx->cur_tau;
+    mb.thr = thr;
+    const double kb0 = ctx->mlp_k_before, ka0 = ctx->mlp_k_after;
+    if ((rc = gw::mlp_batch_hook(ctx, mb))) return rc;
+    // learned skips are not credited as useful work: step C's count is
+    // scaled by the fraction of its reduction length that is still issued
+    if (ctx->mlp_mode == 2 && ctx->mlp_k_before > kb0)
+      fc_scale = (ctx->mlp_k_after - ka0) / (ctx->mlp_k_before - kb0);
+    ctx->stats.kernel_launches += 4;
+  }
   std::vector<int> h_counts((size_t)npt * nqt);
   std::vector<long long> h_kacc((size_t)npt * nqt);
   GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
@@ -824,7 +863,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   ctx->stats.tiles_active += act;
   ctx->stats.slabs_total += (long long)npt * nqt * nslab;
   ctx->stats.slabs_active += sl_act;
-  for (double v : h_fc) fc_host.push_back(v);
+  for (double v : h_fc) fc_host.push_back(v * fc_scale);
   ctx->stats.flops_issued += issued + 2.0 * tile * tile * ksum * prods;
   return GW_OK;
 }
@@ -877,6 +916,10 @@ void gw_destroy(gw_ctx* ctx) {
   free_dev(ctx->d_ri_off);
   free_dev(ctx->d_atom_of_ri);
   free_dev(ctx->d_atom_of_ao);
+  free_dev(ctx->d_mlp_theta);
+  free_dev(ctx->d_mlp_wb);
+  free_dev(ctx->d_mlp_m);
+  free_dev(ctx->d_mlp_v);
   for (cudaEvent_t e : c_events(ctx)) cudaEventDestroy(e);
   c_events(ctx).clear();
   auto& reg = work_registry();
@@ -1053,6 +1096,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->batch_bytes = value;
     return GW_OK;
   }
+  if (!strcmp(key, "mlp_margin")) {
+    if (!std::isfinite(value)) return fail(ctx, GW_ERR_INVALID_ARG, "mlp_margin must be finite");
+    ctx->mlp_margin = value;
+    return GW_OK;
+  }
   if (!strcmp(key, "flush_k")) {
     if (!(value >= 64 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [64, 2^30]");
     ctx->flush_k = (int)value;
@@ -1064,6 +1112,34 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     return GW_OK;
   }
   return fail(ctx, GW_ERR_INVALID_ARG, std::string("unknown option '") + key + "'");
+}
+
+int gw_mlp_log(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision, float* feat_out,
+               float* target_out, long long cap, long long* n_out) {
+  if (!ctx || !n_out || cap < 0 || (cap > 0 && (!feat_out || !target_out))) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (precision != GW_BF16X3 && precision != GW_BF16X6)
+    return fail(ctx, GW_ERR_UNSUPPORTED, "gw_mlp_log: tasks are logged on the tensor-core route");
+  if (tau_count < 0 || tau_first < 0 || tau_first + tau_count > (int)ctx->tau.size())
+    return fail(ctx, GW_ERR_INVALID_ARG, "gw_mlp_log: tau range out of bounds");
+  GW_TRY(cudaSetDevice(ctx->device));
+  double* chi = nullptr;
+  GW_TRY(cudaMalloc(&chi, std::max<size_t>((size_t)tau_count * ctx->nri * ctx->nri, 1) * sizeof(double)));
+  ctx->mlp_log_feat.clear();
+  ctx->mlp_log_tgt.clear();
+  ctx->mlp_mode = 1;
+  int rc = gw_chi_tau(ctx, tau_first, tau_count, thr, precision, GW_SCREEN_BOUND, chi, 1);
+  ctx->mlp_mode = 0;
+  cudaFree(chi);
+  if (rc) return rc;
+  const long long n = (long long)ctx->mlp_log_tgt.size();
+  *n_out = n;
+  const long long m = std::min(n, cap);
+  if (m > 0) {
+    std::memcpy(feat_out, ctx->mlp_log_feat.data(), (size_t)m * gw::kMlpFeatures * sizeof(float));
+    std::memcpy(target_out, ctx->mlp_log_tgt.data(), (size_t)m * sizeof(float));
+  }
+  return GW_OK;
 }
 
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out) {
@@ -1087,10 +1163,18 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown precision");
   if (screening != GW_SCREEN_BOUND && screening != GW_SCREEN_MLP)
     return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown screening mode");
-  if (screening == GW_SCREEN_MLP) return fail(ctx, GW_ERR_UNSUPPORTED, "chi_tau: learned screening not built");
+  const bool tc_prec = precision == GW_BF16X3 || precision == GW_BF16X6;
+  if (screening == GW_SCREEN_MLP && !tc_prec)
+    return fail(ctx, GW_ERR_UNSUPPORTED,
+                "chi_tau: learned screening acts on the tensor-core route (GW_BF16X3 / GW_BF16X6)");
+  if (screening == GW_SCREEN_MLP && !ctx->mlp_ready)
+    return fail(ctx, GW_ERR_ORDER, "chi_tau: learned screening needs gw_mlp_init/gw_mlp_train first");
   if (tau_count > 0 && !chi_out) return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: chi_out is null");
   GW_TRY(cudaSetDevice(ctx->device));
   ctx->stats = gw_stats{};
+  if (ctx->mlp_mode != 1) ctx->mlp_mode = screening == GW_SCREEN_MLP ? 2 : 0;
+  ctx->mlp_skipped = ctx->mlp_seen = 0;
+  ctx->mlp_k_before = ctx->mlp_k_after = 0.0;
   auto t_start = std::chrono::steady_clock::now();
   int rc;
   if ((rc = build_panels(ctx, thr))) return rc;
@@ -1134,6 +1218,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   double ms_g = 0, ms_c = 0;
   for (int j = tau_first; j < tau_first + tau_count; ++j) {
     GW_TRY(cudaEventRecord(ev[0], ctx->stream));
+    ctx->cur_tau = ctx->tau[j];
     gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[j], cso, csv, go, gv,
                       ctx->stream);
     GW_CHECK_LAUNCH();
@@ -1206,6 +1291,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   }
   for (auto& e : ev) cudaEventDestroy(e);
   ctx->stats.flops_useful = ctx->stats.flops_a + ctx->stats.flops_b + ctx->stats.flops_c;
+  ctx->stats.tasks_seen = ctx->mlp_seen;
+  ctx->stats.tasks_skipped = ctx->mlp_skipped;
+  if (ctx->mlp_mode == 2) ctx->mlp_mode = 0;
   ctx->stats.ms_greens = ms_g;
   ctx->stats.ms_step_c = ms_c;
   ctx->stats.ms_total =

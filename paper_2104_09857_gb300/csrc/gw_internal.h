@@ -62,6 +62,28 @@ struct Batch {
 // thr; defined with the chi orchestration.
 int build_panels_for(gw_ctx* ctx, double thr);
 
+// Learned-screening hook of a tensor-core batch, called after the task lists
+// are built and before step C (defined in gw_mlp.cu).  Mode 1 logs
+// (features, log10 contribution norm) of every task; mode 2 drops the tasks
+// the network predicts below thr (minus the margin) from the lists.
+struct MlpBatch {
+  int s0, ns, P0, prow, nslab, npt, nqt, tile, per, pa0, npa, slices;
+  long long Kb;
+  const void* xs;
+  const void* ys;
+  const float* bx2;
+  const float* by2;
+  const unsigned char* bx;
+  const unsigned char* by;
+  int* tasks;
+  int* counts;
+  long long* kacc;
+  const long long* slab_k0;
+  const int* slab_len;
+  double tau, thr;
+};
+int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb);
+
 }  // namespace gw
 
 struct gw_ctx {
@@ -116,6 +138,21 @@ struct gw_ctx {
   long long pt_rows = 0;
   int pt_kmax = 0;
   std::vector<gw::PanelTaskTC> pt_tasks;  // per atom (K == 0: none)
+
+  // learned screening: network (FP32 master, bf16 copy, Adam moments)
+  float* d_mlp_theta = nullptr;
+  void* d_mlp_wb = nullptr;
+  float* d_mlp_m = nullptr;
+  float* d_mlp_v = nullptr;
+  int mlp_step = 0;
+  bool mlp_ready = false;
+  double mlp_margin = 0.5;          // log10 units added to the prediction
+  int mlp_mode = 0;                 // 0 off, 1 log tasks, 2 screen tasks (set per call)
+  std::vector<float> mlp_log_feat;  // logged features / targets (mode 1)
+  std::vector<float> mlp_log_tgt;
+  long long mlp_skipped = 0, mlp_seen = 0;
+  double cur_tau = 0.0;  // tau of the point being computed
+  double mlp_k_before = 0.0, mlp_k_after = 0.0;
 
   // options
   double batch_bytes = 64e9;

@@ -179,7 +179,7 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
     b += al((size_t)prow * Kb * sizeof(double)) + al((size_t)nri * Kb * sizeof(double));
     b += al(ns * sizeof(PanelTask)) + al(R * sizeof(long long)) + al(R * sizeof(int));
     b += al(ns * sizeof(long long));
-    b += al((size_t)ns * n_at * n_at) * 2 + al((size_t)nslab * npt) + al((size_t)nslab * nqt);
+    b += al((size_t)ns * n_at * n_at) * 2 + al((size_t)ns * n_at * npt) + al((size_t)ns * n_at * nqt);
     b += al((size_t)nslab * sizeof(long long)) + al((size_t)nslab * sizeof(int));
     b += al((size_t)npt * nqt * nslab * sizeof(int)) + al((size_t)npt * nqt * sizeof(int)) +
          al((size_t)npt * nqt * sizeof(long long));
@@ -281,8 +281,8 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
     long long* d_seg = bc.take<long long>(ns);
     unsigned char* bx = bc.take<unsigned char>((size_t)ns * n_at * n_at);
     unsigned char* by = bc.take<unsigned char>((size_t)ns * n_at * n_at);
-    unsigned char* fx = bc.take<unsigned char>((size_t)nslab * npt);
-    unsigned char* fy = bc.take<unsigned char>((size_t)nslab * nqt);
+    unsigned char* fx = bc.take<unsigned char>((size_t)ns * n_at * npt);
+    unsigned char* fy = bc.take<unsigned char>((size_t)ns * n_at * nqt);
     long long* d_k0 = bc.take<long long>(nslab);
     int* d_len = bc.take<int>(nslab);
     int* tasks = bc.take<int>((size_t)npt * nqt * nslab);
@@ -337,8 +337,8 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
     // cleared every call: the array keeps the previous call's contents
     NA_TRY(cudaMemsetAsync(X, 0, (size_t)prow * Kb * sizeof(double), st));
     NA_TRY(cudaMemsetAsync(Y, 0, (size_t)nri * Kb * sizeof(double), st));
-    NA_TRY(cudaMemsetAsync(fx, 0, (size_t)nslab * npt, st));
-    NA_TRY(cudaMemsetAsync(fy, 0, (size_t)nslab * nqt, st));
+    NA_TRY(cudaMemsetAsync(fx, 0, (size_t)ns * n_at * npt, st));
+    NA_TRY(cudaMemsetAsync(fy, 0, (size_t)ns * n_at * nqt, st));
     // steps A and B (Eq. 3 brackets), block filter, task lists, step C
     gw::launch_panel_gemm<double>(go, nao, ctx->d_panel64, ctx->d_lam, d_ta, (int)ta.size(), maxNa, 0,
                                   0, nao, b.P0, Kb, nullptr, nullptr, X, st);
@@ -355,7 +355,7 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
                                             d_seg, 0, n_at, n_at, thr, naop, by, fy, nqt, 64, st);
     NA_LAUNCHED();
     gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
-                           counts, kacc, 64, st);
+                           counts, kacc, 64, per, n_at, nao, ctx->d_atom_of_ao, st);
     gw::launch_chi_tiles<double, double>(X, Y, Kb, b.P0, prow, nri, tasks, counts, nslab, npt, nqt,
                                          d_k0, d_len, acc, st);
     NA_LAUNCHED();

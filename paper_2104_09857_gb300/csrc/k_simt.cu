@@ -376,11 +376,10 @@ __global__ void k_operand_block_filter(T* __restrict__ Z, long long ldk, int row
   bool nz = kept && nrm > 0.0;
   if (lane == 0) blockflag[w] = nz;
   if (nz) {
-    int cs = ao_off[m] / kSlabAO, ce = (ao_off[m + 1] - 1) / kSlabAO;
+    // flag (sigma-atom, mu-atom, tile) for every tile the block's rows touch
     int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
-    int nsl = naop / kSlabAO;
-    for (int c = cs + lane; c <= ce; c += 32)
-      for (int tt = ts; tt <= te; ++tt) tileflag[((long long)sl * nsl + c) * ntile + tt] = 1;
+    for (int tt = ts + lane; tt <= te; tt += 32) tileflag[((long long)sl * n_at + m) * ntile + tt] = 1;
+    (void)naop;
   }
 }
 
@@ -391,7 +390,8 @@ __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsign
                               int nslab, int npt, int nqt, int P0, int prow, int nri,
                               const int* __restrict__ atom_of_ri, const int* __restrict__ slab_len,
                               int* __restrict__ tasks, int* __restrict__ counts,
-                              long long* __restrict__ kacc, int tile_rows) {
+                              long long* __restrict__ kacc, int tile_rows, int per, int n_at, int nao,
+                              const int* __restrict__ atom_of_ao) {
   int tile = blockIdx.x;
   int pt = tile / nqt, qt = tile % nqt;
   int pfirst = P0 + pt * tile_rows;
@@ -405,7 +405,19 @@ __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsign
   if (upper) {
     for (int base = 0; base < nslab; base += 32) {
       int s = base + lane;
-      bool on = s < nslab && fx[(long long)s * npt + pt] && fy[(long long)s * nqt + qt];
+      bool on = false;
+      if (s < nslab) {
+        // a slab is a task iff one of its mu atoms has both an X block in the
+        // row tile and a Y block in the column tile (otherwise the product is
+        // exactly zero)
+        const int sl = s / per, c = s % per;
+        const int a_lo = c * kSlabAO;
+        if (a_lo < nao) {
+          const int m0 = atom_of_ao[a_lo], m1 = atom_of_ao[min(nao, a_lo + kSlabAO) - 1];
+          for (int m = m0; m <= m1 && !on; ++m)
+            on = fx[((long long)sl * n_at + m) * npt + pt] && fy[((long long)sl * n_at + m) * nqt + qt];
+        }
+      }
       unsigned m = __ballot_sync(0xffffffffu, on);
       if (on) {
         tasks[(long long)tile * nslab + cnt + __popc(m & ((1u << lane) - 1))] = s;
@@ -540,9 +552,11 @@ template void launch_operand_block_filter<float>(float*, long long, int, const i
 void launch_build_tasks(const unsigned char* fx, const unsigned char* fy, int nslab, int npt,
                         int nqt, int P0, int prow, int nri, const int* atom_of_ri,
                         const int* slab_len, int* tasks, int* counts, long long* kacc,
-                        int tile_rows, cudaStream_t st) {
+                        int tile_rows, int per, int n_at, int nao, const int* atom_of_ao,
+                        cudaStream_t st) {
   k_build_tasks<<<npt * nqt, 32, 0, st>>>(fx, fy, nslab, npt, nqt, P0, prow, nri, atom_of_ri,
-                                          slab_len, tasks, counts, kacc, tile_rows);
+                                          slab_len, tasks, counts, kacc, tile_rows, per, n_at, nao,
+                                          atom_of_ao);
 }
 
 void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int n_at, int pa0,

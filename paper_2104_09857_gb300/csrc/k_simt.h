@@ -29,10 +29,13 @@ void launch_operand_block_filter(T* Z, long long ldk, int rowoff, const int* ri_
                                  const long long* seg, int pa0, int npa, int n_at, double thr,
                                  int naop, unsigned char* blockflag, unsigned char* tileflag,
                                  int ntile, int tile_rows, cudaStream_t st);
+// Occupancy flags are per (sigma-atom of the batch, mu-atom, tile):
+// fx[(sl * n_at + m) * npt + pt], fy[(sl * n_at + m) * nqt + qt].
 void launch_build_tasks(const unsigned char* fx, const unsigned char* fy, int nslab, int npt,
                         int nqt, int P0, int prow, int nri, const int* atom_of_ri,
                         const int* slab_len, int* tasks, int* counts, long long* kacc,
-                        int tile_rows, cudaStream_t st);
+                        int tile_rows, int per, int n_at, int nao, const int* atom_of_ao,
+                        cudaStream_t st);
 void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int n_at, int pa0,
                     int npa, const int* n_ri, const int* n_ao, int s0, double* out, cudaStream_t st);
 template <typename T, typename AccT>

@@ -699,11 +699,10 @@ __global__ void k_slices_block_filter(__nv_bfloat16* __restrict__ Z, int slices,
           Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = __float2bfloat16_rn(0.f);
   }
   if (nz) {
-    const int cs = ao_off[m] / kSlabAO, ce = (ao_off[m + 1] - 1) / kSlabAO;
     const int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
-    const int nsl = naop / kSlabAO;
-    for (int c = cs + lane; c <= ce; c += 32)
-      for (int tt = ts; tt <= te; ++tt) tileflag[(static_cast<long long>(sl) * nsl + c) * ntile + tt] = 1;
+    for (int tt = ts + lane; tt <= te; tt += 32)
+      tileflag[(static_cast<long long>(sl) * n_at + m) * ntile + tt] = 1;
+    (void)naop;
   }
 }
 

@@ -276,18 +276,57 @@ int ensure_panel32(gw_ctx* ctx) {
 // ---------------------------------------------------------------------------
 // batches of owner atoms
 // ---------------------------------------------------------------------------
-std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_bytes) {
+// Batches of consecutive owner atoms under a byte budget for the X and Y
+// operands.  With align_rows > 0 a batch is cut, among the last half of the
+// atoms that fit, where its primary-function count wastes the least of the
+// last align_rows-row tile (step B runs on the batch's rows in such tiles).
+std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_bytes,
+                                int align_rows = 0) {
   std::vector<Batch> out;
   const int n = ctx->n_at;
   int s = 0;
   while (s < n) {
+    int e_max = s;
+    {
+      int P0 = INT32_MAX, P1 = 0;
+      long long K = 0;
+      while (e_max < n) {
+        const PanelDesc& d = ctx->panels[e_max];
+        int q0 = P0, q1 = P1;
+        if (d.K > 0) {
+          q0 = std::min(q0, d.p0);
+          q1 = std::max(q1, d.p0 + d.npw);
+        }
+        const long long K2 = K + (long long)ctx->naop * d.nsig;
+        const double bytes = (double)K2 * ((q1 > q0 ? q1 - q0 : 0) + ctx->nri) * elem_bytes;
+        const bool limit = ctx->batch_atoms > 0 && e_max - s >= ctx->batch_atoms;
+        if (e_max > s && (bytes > budget_bytes || limit)) break;
+        P0 = q0;
+        P1 = q1;
+        K = K2;
+        ++e_max;
+      }
+    }
+    int e_cut = e_max;
+    if (align_rows > 0 && e_max < n) {
+      double best = 2.0;
+      for (int e = e_max; e > s && e >= s + (e_max - s + 1) / 2; --e) {
+        const int R = ctx->ao_off[e] - ctx->ao_off[s];
+        const int Rp = (R + align_rows - 1) / align_rows * align_rows;
+        const double waste = (double)(Rp - R) / Rp;
+        if (waste < best - 1e-12) {
+          best = waste;
+          e_cut = e;
+        }
+      }
+    }
     Batch b{};
     b.s0 = s;
     b.P0 = INT32_MAX;
     b.P1 = 0;
     long long K = 0;
     int e = s;
-    while (e < n) {
+    while (e < e_cut) {
       const PanelDesc& d = ctx->panels[e];
       int P0 = b.P0, P1 = b.P1;
       if (d.K > 0) {
@@ -295,9 +334,6 @@ std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_by
         P1 = std::max(P1, d.p0 + d.npw);
       }
       long long K2 = K + (long long)ctx->naop * d.nsig;
-      double bytes = (double)K2 * ((P1 > P0 ? P1 - P0 : 0) + ctx->nri) * elem_bytes;
-      bool limit = ctx->batch_atoms > 0 && e - s >= ctx->batch_atoms;
-      if (e > s && (bytes > budget_bytes || limit)) break;
       b.P0 = P0;
       b.P1 = P1;
       b.seg.push_back(K);
@@ -1190,7 +1226,8 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   // device bytes per operand element: FP64, FP32, or FP32 plus bf16 slices
   const size_t esz = f64 ? sizeof(double)
                          : precision == GW_BF16X6 ? 6 : precision == GW_BF16X3 ? 4 : sizeof(float);
-  std::vector<Batch> batches = plan_batches(ctx, esz, ctx->batch_bytes);
+  std::vector<Batch> batches =
+      plan_batches(ctx, esz, ctx->batch_bytes, tcpath ? gw::tc_tile_rows() : 0);
   ctx->stats.n_batches = (int)batches.size();
 
   double *cso, *csv, *go, *gv, *acc, *stage;

@@ -155,7 +155,7 @@ struct gw_ctx {
   double mlp_k_before = 0.0, mlp_k_after = 0.0;
 
   // options
-  double batch_bytes = 64e9;
+  double batch_bytes = 40e9;
   int batch_atoms = 0;
   int flush_k = 256;
   int last_precision = -1;  // tensor-core step C: FP32 accumulator drained every flush_k elements

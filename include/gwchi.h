@@ -128,8 +128,11 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
  * (real, phases removed as for chi; W even in tau; RI metric = identity).
  * W_tau[n_tau][n_ri][n_ri]: device if w_on_device else host (e.g. the output
  * of gw_chi_to_w).  Filter: 3c, G and (mu-atom, P-atom) blocks of B^n with
- * norm < thr are dropped.  precision: GW_FP64 only.  sigma_out: host,
- * [n_orb][n_tau][2].  Uses the tensor, orbitals and tau grid of the context. */
+ * norm < thr are dropped.  precision: GW_FP64 (CUDA cores) or GW_BF16X3 /
+ * GW_BF16X6 (the two products B W and (B W) B^T on the tensor cores as split-
+ * bf16 tile jobs with FP64 outputs; G, B^n and the traces stay FP64).
+ * sigma_out: host, [n_orb][n_tau][2].  Uses the tensor, orbitals and tau grid
+ * of the context. */
 int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
                  int n_orb, double thr, int precision, double* sigma_out);
 

@@ -14,6 +14,7 @@
 #include "gw_internal.h"
 #include "k_chain.h"
 #include "k_simt.h"
+#include "k_tc.h"
 
 namespace gw {
 namespace sigma {
@@ -118,10 +119,12 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
     ctx->err = "gw_sigma_tau: bad arguments";
     return GW_ERR_INVALID_ARG;
   }
-  if (precision != GW_FP64) {
-    ctx->err = "gw_sigma_tau: only GW_FP64 is available for the self-energy";
+  if (precision != GW_FP64 && precision != GW_BF16X3 && precision != GW_BF16X6) {
+    ctx->err = "gw_sigma_tau: precision must be GW_FP64, GW_BF16X3 or GW_BF16X6";
     return GW_ERR_UNSUPPORTED;
   }
+  const bool mixed = precision != GW_FP64;
+  const int slices = precision == GW_BF16X6 ? 3 : 2;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at, n_tau = (int)ctx->tau.size();
   for (int a = 0; a < n_orb; ++a)
     if (orbitals[a] < 0 || orbitals[a] >= nao) {
@@ -189,6 +192,61 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
   SG_TRY(cudaMalloc(&b_part.p, (size_t)kDotBlocks * 2 * 8));
   double *y = (double*)b_y.p, *z = (double*)b_z.p, *go = (double*)b_go.p, *gv = (double*)b_gv.p;
   std::vector<double> part((size_t)kDotBlocks * 2);
+  // tensor-core route: both products as step-C style tile jobs on bf16 slices
+  //   y = -(B W)     (rows mu, columns Q, K = P)
+  //   z = -(y B^T)   (rows mu, columns nu, K = Q)  = B W B^T
+  const int tile = gw::tc_tile_rows();
+  const int kpad = (nri + 63) / 64 * 64;
+  DevBuf b_bs, b_ws, b_ys, b_tl1, b_tk1, b_ct1, b_k01, b_ln1, b_tl2, b_tk2, b_ct2, b_err;
+  int nslab = 0, n_tiles1 = 0, n_tiles2 = 0, nqt1 = 0, nqt2 = 0;
+  CUtensorMap m_b, m_w, m_y, m_bq;
+  if (mixed) {
+    const int slab = 512;
+    nslab = (kpad + slab - 1) / slab;
+    std::vector<long long> k0(nslab);
+    std::vector<int> len(nslab);
+    for (int i = 0; i < nslab; ++i) {
+      k0[i] = (long long)i * slab;
+      len[i] = std::min(slab, kpad - i * slab);
+    }
+    const int npt = (nao + tile - 1) / tile;
+    nqt1 = (nri + tile - 1) / tile;
+    nqt2 = (nao + tile - 1) / tile;
+    n_tiles1 = npt * nqt1;
+    n_tiles2 = npt * nqt2;
+    auto lists = [&](int nt, DevBuf& tl, DevBuf& tk, DevBuf& ct) -> int {
+      std::vector<int> h_tl(nt), h_tk((size_t)nt * nslab), h_ct(nt, nslab);
+      for (int t = 0; t < nt; ++t) {
+        h_tl[t] = t;
+        for (int i = 0; i < nslab; ++i) h_tk[(size_t)t * nslab + i] = i;
+      }
+      SG_TRY(cudaMalloc(&tl.p, nt * sizeof(int)));
+      SG_TRY(cudaMalloc(&tk.p, h_tk.size() * sizeof(int)));
+      SG_TRY(cudaMalloc(&ct.p, nt * sizeof(int)));
+      SG_TRY(cudaMemcpy(tl.p, h_tl.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+      SG_TRY(cudaMemcpy(tk.p, h_tk.data(), h_tk.size() * sizeof(int), cudaMemcpyHostToDevice));
+      SG_TRY(cudaMemcpy(ct.p, h_ct.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+      return GW_OK;
+    };
+    if ((rc = lists(n_tiles1, b_tl1, b_tk1, b_ct1))) return rc;
+    if ((rc = lists(n_tiles2, b_tl2, b_tk2, b_ct2))) return rc;
+    SG_TRY(cudaMalloc(&b_k01.p, nslab * sizeof(long long)));
+    SG_TRY(cudaMalloc(&b_ln1.p, nslab * sizeof(int)));
+    SG_TRY(cudaMemcpy(b_k01.p, k0.data(), nslab * sizeof(long long), cudaMemcpyHostToDevice));
+    SG_TRY(cudaMemcpy(b_ln1.p, len.data(), nslab * sizeof(int), cudaMemcpyHostToDevice));
+    SG_TRY(cudaMalloc(&b_bs.p, (size_t)slices * nao * kpad * 2));
+    SG_TRY(cudaMalloc(&b_ws.p, (size_t)slices * nri * kpad * 2));
+    SG_TRY(cudaMalloc(&b_ys.p, (size_t)slices * nao * kpad * 2));
+    SG_TRY(cudaMalloc(&b_err.p, sizeof(int)));
+    SG_TRY(cudaMemsetAsync(b_err.p, 0, sizeof(int), st));
+    if (gw::make_slice_map(&m_b, b_bs.p, kpad, nao, slices, tile) ||
+        gw::make_slice_map(&m_w, b_ws.p, kpad, nri, slices, tile) ||
+        gw::make_slice_map(&m_y, b_ys.p, kpad, nao, slices, tile)) {
+      ctx->err = "gw_sigma_tau: cuTensorMapEncodeTiled failed";
+      return GW_ERR_CUDA;
+    }
+    m_bq = m_b;
+  }
   for (int jt = 0; jt < n_tau; ++jt) {
     gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[jt], (double*)b_cso.p,
                       (double*)b_csv.p, go, gv, st);
@@ -199,8 +257,30 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
     const double* wt = w + (size_t)jt * nn_ri;
     for (int a = 0; a < n_orb; ++a) {
       const double* b = bn + (size_t)a * nao * nri;
-      gw::chain_dgemm(false, false, nao, nri, nri, 1.0, b, nri, wt, nri, 0.0, y, nri, st);  // Y = B W
-      gw::chain_dgemm(false, true, nao, nao, nri, 1.0, y, nri, b, nri, 0.0, z, nao, st);    // Z = Y B^T
+      if (!mixed) {
+        gw::chain_dgemm(false, false, nao, nri, nri, 1.0, b, nri, wt, nri, 0.0, y, nri, st);  // Y = B W
+        gw::chain_dgemm(false, true, nao, nao, nri, 1.0, y, nri, b, nri, 0.0, z, nao, st);    // Z = Y B^T
+      } else {
+        gw::launch_split_f64(b, nri, nao, nri, kpad, slices, b_bs.p, st);
+        gw::launch_split_f64(wt, nri, nri, nri, kpad, slices, b_ws.p, st);
+        SG_TRY(cudaMemsetAsync(y, 0, (size_t)nao * nri * 8, st));
+        if (gw::launch_chi_tc(slices, m_b, m_w, (const int*)b_tl1.p, n_tiles1, (const int*)b_tk1.p,
+                              (const int*)b_ct1.p, nslab, (const long long*)b_k01.p,
+                              (const int*)b_ln1.p, 0, nao, nri, nqt1, y, ctx->flush_k, (int*)b_err.p, st)) {
+          ctx->err = "gw_sigma_tau: tensor-core launch setup failed";
+          return GW_ERR_CUDA;
+        }
+        // y holds -(B W); its slices are the row operand of the second product
+        gw::launch_split_f64(y, nri, nao, nri, kpad, slices, b_ys.p, st);
+        SG_TRY(cudaMemsetAsync(z, 0, nn_ao * 8, st));
+        if (gw::launch_chi_tc(slices, m_y, m_bq, (const int*)b_tl2.p, n_tiles2, (const int*)b_tk2.p,
+                              (const int*)b_ct2.p, nslab, (const long long*)b_k01.p,
+                              (const int*)b_ln1.p, 0, nao, nao, nqt2, z, ctx->flush_k, (int*)b_err.p, st)) {
+          ctx->err = "gw_sigma_tau: tensor-core launch setup failed";
+          return GW_ERR_CUDA;
+        }
+        SG_TRY(cudaGetLastError());
+      }
       gw::sigma::k_dot2<<<kDotBlocks, 256, 0, st>>>(go, gv, z, (long long)nn_ao, (double*)b_part.p);
       SG_TRY(cudaGetLastError());
       SG_TRY(cudaMemcpyAsync(part.data(), b_part.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -212,6 +292,14 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
       }
       sigma_out[((size_t)a * n_tau + jt) * 2 + 0] = -so;
       sigma_out[((size_t)a * n_tau + jt) * 2 + 1] = sv;
+    }
+  }
+  if (mixed) {
+    int h_err = 0;
+    SG_TRY(cudaMemcpy(&h_err, b_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_err) {
+      ctx->err = "gw_sigma_tau: a bounded wait of the tensor-core kernel gave up";
+      return GW_ERR_TIMEOUT;
     }
   }
   return GW_OK;

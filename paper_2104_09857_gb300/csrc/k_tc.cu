@@ -706,7 +706,35 @@ __global__ void k_slices_block_filter(__nv_bfloat16* __restrict__ Z, int slices,
   }
 }
 
+// FP64 [rows][cols] (row stride ld) -> bf16 slices [S][rows][kpad], zero for
+// k >= cols
+__global__ void k_split_f64(const double* __restrict__ a, long long ld, int rows, int cols, int kpad,
+                            int slices, __nv_bfloat16* __restrict__ out) {
+  const long long n = static_cast<long long>(rows) * kpad;
+  const long long slice = n;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i / kpad), k = static_cast<int>(i % kpad);
+    double v = k < cols ? a[static_cast<long long>(r) * ld + k] : 0.0;
+    for (int s = 0; s < slices; ++s) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      out[s * slice + i] = h;
+      v -= static_cast<double>(__bfloat162float(h));
+    }
+  }
+}
+
 }  // namespace tc
+
+void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
+                      void* out, cudaStream_t st) {
+  const long long n = static_cast<long long>(rows) * kpad;
+  if (n == 0) return;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  tc::k_split_f64<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a, ld, rows, cols, kpad, slices,
+                                                                static_cast<__nv_bfloat16*>(out));
+}
 
 // ---------------------------------------------------------------------------
 // host side

@@ -30,6 +30,10 @@ int launch_panel_tc(int slices, const CUtensorMap& mg, const CUtensorMap& mp, co
                     const int* rowmul, const int* row_slocal, float* norm2, const int* atom_of_ri,
                     const int* atom_of_ao, int n_at, int npa, int pa0, int flush_k, int* err_flag,
                     cudaStream_t st);
+// FP64 [rows][cols] (row stride ld) -> `slices` bf16 slices [S][rows][kpad],
+// zero-padded in k.
+void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
+                      void* out, cudaStream_t st);
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
                      int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
                      long long slice_elems, void* out, cudaStream_t st);

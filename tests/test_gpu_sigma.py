@@ -59,3 +59,20 @@ def test_chi_w_sigma_chain_on_device(pkg):
         w = ctx.chi_to_w(chi, v, gamma, delta)
         got = ctx.sigma_tau(w, orbs, case.thr)
     assert np.abs(got - s_ref).max() <= 1e-9 * np.abs(s_ref).max()
+
+
+@pytest.mark.parametrize("name", ["benzene", "ribbon28"])
+def test_sigma_bf16x6_matches_oracle(pkg, name):
+    """The two products of Eq. 10 on the tensor cores (split bf16, 6 products):
+    within the 1e-6 mixed-precision bar of the oracle."""
+    case = make_case(name, n_tau=3)
+    w = synthetic_w(case.system.nri_total, case.tau, 9)
+    orbs = [case.n_occ - 1, case.n_occ]
+    ref = osg.sigma_dense(case, w, orbs, thr=case.thr)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        got = ctx.sigma_tau(w, orbs, case.thr, precision="bf16x6")
+        fp64 = ctx.sigma_tau(w, orbs, case.thr, precision="fp64")
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-6 * scale
+    assert np.abs(fp64 - ref).max() <= 1e-10 * scale

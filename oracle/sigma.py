@@ -71,3 +71,45 @@ def sigma_mo(t: np.ndarray, C: np.ndarray, eps: np.ndarray, n_occ: int, mu_fermi
     s_occ = float(np.sum(np.exp(e[:n_occ] * tau) * q[:n_occ]))
     s_virt = float(np.sum(np.exp(-e[n_occ:] * tau) * q[n_occ:]))
     return -s_occ, s_virt
+
+
+def b_half_blocks(case, n: int, thr: float) -> np.ndarray:
+    """B^n[mu][P] = sum_nu C[nu][n] (nu mu|P) from the stored atom blocks
+    (no dense 3c tensor), with the 3c and B^n block filters of sigma_dense."""
+    s = case.system
+    ao = oc.offsets(s.n_ao)
+    ri = oc.offsets(s.n_ri)
+    t3 = case.t3c
+    c = case.C[:, n]
+    b = np.zeros((ao[-1], ri[-1]))
+    for i, (a, bb, p) in enumerate(t3.blocks):
+        blk = t3.data[t3.offsets[i]:t3.offsets[i + 1]].reshape(s.n_ao[a], s.n_ao[bb], s.n_ri[p])
+        if thr > 0.0 and np.sqrt(np.sum(blk * blk)) < thr:
+            continue
+        # (nu in A, mu in B): B[mu][P] += C[nu] blk[nu][mu][P]
+        b[ao[bb]:ao[bb + 1], ri[p]:ri[p + 1]] += np.einsum("v,vmp->mp", c[ao[a]:ao[a + 1]], blk)
+        if a != bb:
+            # (nu in B, mu in A): T[nu][mu][P] = blk[mu][nu][P]
+            b[ao[a]:ao[a + 1], ri[p]:ri[p + 1]] += np.einsum("v,mvp->mp", c[ao[bb]:ao[bb + 1]], blk)
+    if thr > 0.0:
+        nrm = np.sqrt(oc.block_sq_sums(b, [ao, ri]))
+        keep = np.repeat(np.repeat(nrm >= thr, np.diff(ao), 0), np.diff(ri), 1)
+        b = np.where(keep, b, 0.0)
+    return b
+
+
+def sigma_blocks(case, w_tau: np.ndarray, orbitals, tau_indices, thr: float | None = None) -> np.ndarray:
+    """Like sigma_dense for the given tau indices, without the dense 3c tensor
+    (for systems of a few hundred basis functions and more)."""
+    thr = case.thr if thr is None else thr
+    ao = oc.offsets(case.system.n_ao)
+    out = np.zeros((len(orbitals), len(tau_indices), 2))
+    for a, n in enumerate(orbitals):
+        b = b_half_blocks(case, n, thr)
+        for jj, j in enumerate(tau_indices):
+            go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, case.tau[j])
+            go = oc.filter_sym_2d(go, ao, thr)
+            gv = oc.filter_sym_2d(gv, ao, thr)
+            out[a, jj, 0] = -s_term(go, b, w_tau[j])
+            out[a, jj, 1] = s_term(gv, b, w_tau[j])
+    return out

@@ -21,6 +21,8 @@ from .systems import (
     random_cluster,
     species_basis,
     tiny_chain,
+    carbon_ring_with_h,
+    molecule_set,
 )
 from .tensors import (
     ThreeCenter,
@@ -29,6 +31,7 @@ from .tensors import (
     orbitals_from_hamiltonian,
     log_tau_grid,
     make_case,
+    case_from_system,
     Case,
 )
 
@@ -41,6 +44,9 @@ __all__ = [
     "random_cluster",
     "species_basis",
     "tiny_chain",
+    "carbon_ring_with_h",
+    "molecule_set",
+    "case_from_system",
     "ThreeCenter",
     "make_three_center",
     "make_hamiltonian",

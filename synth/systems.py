@@ -141,3 +141,29 @@ def random_cluster(n_atoms: int, density: float, min_dist: float, seed: int,
     sp = uniform_stream(seed, 2, 0, n_atoms)
     species = ["C" if s < p_carbon else "H" for s in sp]
     return System(f"cluster-{n_atoms}", pts, species)
+
+
+def carbon_ring_with_h(n_atoms: int) -> System:
+    """Planar ring: n_c carbons 1.4 A apart on a circle, an H 1.09 A radially
+    outside every other carbon (C:H = 2:1); n_atoms = n_c + n_c // 2."""
+    n_c = max(3, int(round(n_atoms * 2 / 3)))
+    radius = CC_BOND / (2.0 * np.sin(np.pi / n_c))
+    ang = 2.0 * np.pi * np.arange(n_c) / n_c
+    c = np.stack([radius * np.cos(ang), radius * np.sin(ang), np.zeros(n_c)], axis=1)
+    hi = np.arange(0, n_c, 2)
+    h = np.stack([(radius + CH_BOND) * np.cos(ang[hi]), (radius + CH_BOND) * np.sin(ang[hi]),
+                  np.zeros(len(hi))], axis=1)
+    return System(f"ring-{n_c + len(hi)}", np.concatenate([c, h]), ["C"] * n_c + ["H"] * len(hi))
+
+
+def molecule_set(n_mol: int, lo: int, hi: int, seed: int) -> list[System]:
+    """n_mol molecules with atom counts uniform on [lo, hi]: odd index a
+    ribbon segment (cells chosen to reach the count), even index a ring."""
+    counts = lo + np.floor(uniform_stream(seed, 3, 0, n_mol) * (hi - lo + 1)).astype(int)
+    out = []
+    for i, n in enumerate(counts):
+        if i % 2 == 1:
+            out.append(armchair_ribbon(max(1.0, n / 12.0)))
+        else:
+            out.append(carbon_ring_with_h(int(n)))
+    return out

@@ -167,6 +167,15 @@ CASES = {
 }
 
 
+def case_from_system(sysm: System, n_tau: int, thr: float, seed: int) -> Case:
+    """A Case for an arbitrary system with the standard recipe."""
+    n_occ = max(1, min(sysm.n_electrons // 2, sysm.nao_total - 1))
+    t3c = make_three_center(sysm, thr, seed)
+    h = make_hamiltonian(sysm, seed)
+    c, eps = orbitals_from_hamiltonian(h, n_occ)
+    return Case(sysm.name, sysm, t3c, c, eps, n_occ, 0.0, log_tau_grid(n_tau), thr, seed)
+
+
 def make_case(name: str, n_tau: int | None = None, thr: float | None = None,
               seed: int | None = None, n_occ: int | None = None) -> Case:
     builder, nt, th, sd = CASES[name]

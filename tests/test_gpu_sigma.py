@@ -76,3 +76,33 @@ def test_sigma_bf16x6_matches_oracle(pkg, name):
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-6 * scale
     assert np.abs(fp64 - ref).max() <= 1e-10 * scale
+
+
+def test_uneven_molecule_set_mixed_and_fp64(pkg):
+    """Self-energy (HOMO, LUMO) of molecules of uneven size drawn like the
+    batched self-energy workload (rings and ribbon segments, 10-150 atoms,
+    thr 1e-9): per-molecule error of BF16x6 and FP64 against the block oracle
+    on three of the twenty tau points."""
+    from synth import case_from_system, molecule_set
+
+    mols = molecule_set(64, 10, 150, 20210425)
+    sizes = np.array([m.n_atoms for m in mols])
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.argsort(sizes)[32]),
+            int(np.argsort(sizes)[16])]
+    taus = [0, 9, 19]
+    for i in pick:
+        case = case_from_system(mols[i], 20, 1e-9, 20210425 + i)
+        w = synthetic_w(case.system.nri_total, case.tau, 100 + i)
+        orbs = [case.n_occ - 1, case.n_occ]
+        ref = osg.sigma_blocks(case, w, orbs, taus)
+        with pkg.Context(0) as ctx:
+            ctx.load_case(case)
+            mixed = ctx.sigma_tau(w, orbs, case.thr, precision="bf16x6")[:, taus]
+            fp64 = ctx.sigma_tau(w, orbs, case.thr, precision="fp64")[:, taus]
+        scale = np.abs(ref).max()
+        e_mixed = np.abs(mixed - ref).max() / scale
+        e_fp64 = np.abs(fp64 - ref).max() / scale
+        print(f"{case.system.name}: {case.system.n_atoms} atoms, bf16x6 err {e_mixed:.2e}, "
+              f"fp64 err {e_fp64:.2e}")
+        assert e_mixed <= 1e-6
+        assert e_fp64 <= 1e-10

@@ -57,3 +57,23 @@ def test_filter_threshold_zero_and_tiny_agree(setup):
     a = osg.sigma_dense(case, w, orbs, thr=0.0)
     b = osg.sigma_dense(case, w, orbs, thr=1e-300)
     assert np.array_equal(a, b)
+
+
+def test_block_route_equals_dense_route(setup):
+    """B^n from the stored blocks equals the dense half transform (both filters)."""
+    case, t, w, orbs = setup
+    for thr in (0.0, 1e-2):
+        a = osg.sigma_dense(case, w, orbs, thr=thr)
+        b = osg.sigma_blocks(case, w, orbs, list(range(len(case.tau))), thr=thr)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14 * np.abs(a).max())
+
+
+def test_molecule_set_shapes():
+    from synth import molecule_set
+
+    mols = molecule_set(8, 10, 150, 20210425)
+    assert len(mols) == 8
+    for m in mols:
+        assert 8 <= m.n_atoms <= 160
+        nc = m.species.count("C")
+        assert abs(nc - 2 * (m.n_atoms - nc)) <= 4  # about 2:1

@@ -47,8 +47,13 @@ enum gw_precision {
   GW_FP32 = 1,   /* FP32 operands, FP32 accumulation per block slab (CUDA cores)   */
   GW_BF16X3 = 2, /* two-term BF16 split, 3 products per product, FP32 accumulation
                     on the tensor cores (tcgen05)                                  */
-  GW_BF16X6 = 3  /* three-term BF16 split, 6 products per product, FP32
+  GW_BF16X6 = 3, /* three-term BF16 split, 6 products per product, FP32
                     accumulation on the tensor cores (tcgen05)                     */
+  GW_FP16X3 = 4  /* two-term binary16 split of each operand scaled by a power of
+                    two (from a bound on its magnitude: no overflow), 3 products
+                    per product, FP32 accumulation on the tensor cores; 22
+                    significant bits per operand against 24 for GW_BF16X6, at
+                    half the products and two thirds of the operand bytes      */
 };
 
 enum gw_screening {
@@ -129,8 +134,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
  * W_tau[n_tau][n_ri][n_ri]: device if w_on_device else host (e.g. the output
  * of gw_chi_to_w).  Filter: 3c, G and (mu-atom, P-atom) blocks of B^n with
  * norm < thr are dropped.  precision: GW_FP64 (CUDA cores) or GW_BF16X3 /
- * GW_BF16X6 (the two products B W and (B W) B^T on the tensor cores as split-
- * bf16 tile jobs with FP64 outputs; G, B^n and the traces stay FP64).
+ * GW_BF16X6 / GW_FP16X3 (the two products B W and (B W) B^T on the tensor
+ * cores as split 16-bit tile jobs with FP64 outputs; G, B^n and the traces
+ * stay FP64).
  * sigma_out: host, [n_orb][n_tau][2].  Uses the tensor, orbitals and tau grid
  * of the context. */
 int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
@@ -219,7 +225,21 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
 
 /* Tuning knobs (no effect on results beyond rounding order):
  *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
- *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)        */
+ *                  (default 40e9)
+ *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)
+ *   "flush_k"      split forms: reduction elements between drains of the
+ *                  tensor cores' main FP32 accumulator (rounded down to a
+ *                  multiple of 16, default 64; each 16-element MMA step of the
+ *                  accumulation loses about half an ulp toward zero)
+ *   "c_split_k"    split forms: step-C work units cover about this many
+ *                  reduction elements of one 128 x 128 chi tile and add into
+ *                  chi with FP64 atomics, so the summation order (and the
+ *                  last bits) vary from run to run; 0 = one unit per tile,
+ *                  bitwise reproducible (default 2048)
+ *   "c_order"      with c_split_k = 0: tile order, 0 longest first (default),
+ *                  1 grouped raster
+ *   "mlp_margin"   learned screening: decades added to the predicted norm
+ * Unknown keys and out-of-range values return GW_ERR_INVALID_ARG.            */
 int gw_set_option(gw_ctx* ctx, const char* key, double value);
 
 #ifdef __cplusplus

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgwchi.so")
 
 GW_OK = 0
-GW_FP64, GW_FP32, GW_BF16X3, GW_BF16X6 = 0, 1, 2, 3
+GW_FP64, GW_FP32, GW_BF16X3, GW_BF16X6, GW_FP16X3 = 0, 1, 2, 3, 4
 GW_SCREEN_BOUND, GW_SCREEN_MLP = 0, 1
 
 ERRORS = {
@@ -31,7 +31,8 @@ ERRORS = {
     -9: "GW_ERR_UNSUPPORTED",
 }
 
-PRECISIONS = {"fp64": GW_FP64, "fp32": GW_FP32, "bf16x3": GW_BF16X3, "bf16x6": GW_BF16X6}
+PRECISIONS = {"fp64": GW_FP64, "fp32": GW_FP32, "bf16x3": GW_BF16X3, "bf16x6": GW_BF16X6,
+              "fp16x3": GW_FP16X3}
 
 
 class GwError(RuntimeError):

@@ -568,8 +568,9 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
 // ---------------------------------------------------------------------------
 // tensor-core route: transposed split panels (once per thr and slice count)
 // ---------------------------------------------------------------------------
-int ensure_pt(gw_ctx* ctx, int slices) {
-  if (ctx->pt_ok && ctx->pt_slices == slices && ctx->pt_thr == ctx->panels_thr) return GW_OK;
+int ensure_pt(gw_ctx* ctx, int slices, int f16) {
+  if (ctx->pt_ok && ctx->pt_slices == slices && ctx->pt_f16 == f16 && ctx->pt_thr == ctx->panels_thr)
+    return GW_OK;
   free_dev(ctx->d_pt);
   ctx->d_pt = nullptr;
   ctx->pt_ok = false;
@@ -608,13 +609,30 @@ int ensure_pt(gw_ctx* ctx, int slices) {
   gw::PanelTaskTC* d_list;
   int rc;
   if ((rc = upload(ctx, "pt_list", list, &d_list))) return rc;
+  double pt_scale = 1.0;
+  if (f16) {
+    // exact max |T| over the panels (viewed as rows of 1024 plus a tail)
+    double *st2, h[4] = {0, 0, 0, 0};
+    if ((rc = wsT(ctx, "pt_absmax", 4, &st2))) return rc;
+    const long long n = ctx->panel_elems, nrow = n / 1024;
+    gw::launch_absmax_rowsum(ctx->d_panel64, 1024, (int)nrow, 1024, st2, ctx->stream);
+    gw::launch_absmax_rowsum(ctx->d_panel64 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
+                             (int)(n - nrow * 1024), st2 + 2, ctx->stream);
+    GW_CHECK_LAUNCH();
+    GW_TRY(cudaMemcpyAsync(h, st2, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    GW_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->t_absmax = std::max(h[0], h[2]);
+    pt_scale = gw::pow2_scale(ctx->t_absmax);
+  }
   gw::launch_transpose_panels(ctx->d_panel64, d_list, (int)list.size(), max_npad, kmax, slices,
-                              rows * kmax, ctx->d_pt, ctx->stream);
+                              rows * kmax, f16, pt_scale, ctx->d_pt, ctx->stream);
   GW_CHECK_LAUNCH();
   GW_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->pt_rows = rows;
   ctx->pt_kmax = kmax;
   ctx->pt_slices = slices;
+  ctx->pt_f16 = f16;
+  ctx->pt_scale = pt_scale;
   ctx->pt_thr = ctx->panels_thr;
   ctx->pt_ok = true;
   return GW_OK;
@@ -626,8 +644,13 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
                      double thr, double* acc, std::vector<double>& fc_host, int precision,
                      size_t batch_idx) {
   const int slices = precision == GW_BF16X6 ? 3 : 2;
+  const int f16 = precision == GW_FP16X3;
   const double prods = slices == 3 ? 6.0 : 3.0;
   const int tile = gw::tc_tile_rows();
+  // binary16 scales (powers of two; 1 for bf16): G^occ, G^virt, X, Y, T
+  const double s_go = f16 ? ctx->tc_scale[0] : 1.0, s_gv = f16 ? ctx->tc_scale[1] : 1.0;
+  const double s_x = f16 ? ctx->tc_scale[2] : 1.0, s_y = f16 ? ctx->tc_scale[3] : 1.0;
+  const double s_t = f16 ? ctx->pt_scale : 1.0;
   const int ns = b.s1 - b.s0;
   const int prow = b.P1 - b.P0;
   const long long Kb = b.Kb;
@@ -657,7 +680,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
   GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
   CUtensorMap mp;
-  if (gw::make_slice_map(&mp, ctx->d_pt, kmax, ctx->pt_rows, slices, tile))
+  if (gw::make_slice_map(&mp, ctx->d_pt, kmax, ctx->pt_rows, slices, tile, f16))
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
   double issued = 0.0;
   cudaEvent_t ea0, ea1;
@@ -677,7 +700,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       t.s_local = s - b.s0;
       const int ntn = (t.N + tile - 1) / tile;
       for (int nt = 0; nt < ntn; ++nt)
-        for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), mt, nt, 0));
+        for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), nt, mt, 0));
       issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
       ta.push_back(t);
     }
@@ -690,14 +713,16 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       const long long g_elems = (long long)ta.size() * rows_a * kmax;
       if ((rc = ws(ctx, "GgA", (size_t)slices * g_elems * 2, &gg))) return rc;
       gw::launch_gather_g(g_occ, nao, d_ta, (int)ta.size(), ctx->d_lam, 0, nao, rows_a, kmax, slices,
-                          g_elems, gg, ctx->stream);
+                          g_elems, f16, s_go, gg, ctx->stream);
       GW_CHECK_LAUNCH();
       CUtensorMap mg;
-      if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile))
+      if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step A)");
-      if (gw::launch_panel_tc(slices, mg, mp, d_tiles, (int)tiles.size(), d_ta, 0, nao, xs,
+      if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
+                              (int)tiles.size(), d_ta, 0, nao, xs,
                               (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
-                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, n_at, npa, pa0, ctx->flush_k,
+                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, npa, pa0,
+                              ctx->flush_k,
                               d_err, ctx->stream))
         return fail(ctx, GW_ERR_CUDA, "tensor-core step A launch setup failed");
       GW_CHECK_LAUNCH();
@@ -743,14 +768,16 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       const long long g_elems = (long long)tb.size() * rows_b * kmax;
       if ((rc = ws(ctx, "GgB", (size_t)slices * g_elems * 2, &gg))) return rc;
       gw::launch_gather_g(g_virt, nao, d_tb, (int)tb.size(), ctx->d_lam, r0, R, rows_b, kmax, slices,
-                          g_elems, gg, ctx->stream);
+                          g_elems, f16, s_gv, gg, ctx->stream);
       GW_CHECK_LAUNCH();
       CUtensorMap mg;
-      if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile))
+      if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
-      if (gw::launch_panel_tc(slices, mg, mp, d_tiles, (int)tiles.size(), d_tb, 1, R, ys,
+      if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
+                              (int)tiles.size(), d_tb, 1, R, ys,
                               (long long)nri * Kb, Kb, 0, d_rowbase, d_rowmul, d_rowsl, by2,
-                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, n_at, n_at, 0, ctx->flush_k,
+                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, n_at, 0,
+                              ctx->flush_k,
                               d_err, ctx->stream))
         return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
       GW_CHECK_LAUNCH();
@@ -823,6 +850,9 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     mb.pa0 = pa0;
     mb.npa = npa;
     mb.slices = slices;
+    mb.f16 = f16;
+    mb.xinv = (float)(1.0 / s_x);
+    mb.yinv = (float)(1.0 / s_y);
     mb.Kb = Kb;
     mb.xs = xs;
     mb.ys = ys;
@@ -852,24 +882,96 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   GW_TRY(cudaMemcpyAsync(h_kacc.data(), kacc, h_kacc.size() * sizeof(long long),
                          cudaMemcpyDeviceToHost, ctx->stream));
   GW_TRY(cudaStreamSynchronize(ctx->stream));
-  // active tiles, longest first (static round-robin over persistent CTAs)
+  // active tiles in the order the persistent CTAs take them round-robin:
+  // longest first (c_order 0), or grouped raster (c_order 1: groups of 8 row
+  // tiles swept along the columns, so that CTAs running side by side share
+  // operand tiles in L2)
   std::vector<int> active;
   for (size_t t = 0; t < h_counts.size(); ++t)
     if (h_counts[t] > 0) active.push_back((int)t);
-  std::stable_sort(active.begin(), active.end(),
-                   [&](int a, int c) { return h_kacc[a] > h_kacc[c]; });
-  int* d_active;
-  if ((rc = upload(ctx, "active_tiles", active, &d_active))) return rc;
+  if (ctx->c_order == 1) {
+    std::stable_sort(active.begin(), active.end(), [&](int a, int c) {
+      const int pa = a / nqt, qa = a % nqt, pc = c / nqt, qc = c % nqt;
+      if (pa / 8 != pc / 8) return pa / 8 < pc / 8;
+      if (qa != qc) return qa < qc;
+      return pa < pc;
+    });
+  } else {
+    std::stable_sort(active.begin(), active.end(),
+                     [&](int a, int c) { return h_kacc[a] > h_kacc[c]; });
+  }
   CUtensorMap mx, my;
-  if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile) ||
-      gw::make_slice_map(&my, ys, Kb, nri, slices, tile))
+  if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile, f16) ||
+      gw::make_slice_map(&my, ys, Kb, nri, slices, tile, f16))
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
   cudaEvent_t ec0, ec1;
   if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
-  GW_TRY(cudaEventRecord(ec0, ctx->stream));
-  if (gw::launch_chi_tc(slices, mx, my, d_active, (int)active.size(), tasks, counts, nslab, d_k0,
-                        d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
-    return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+  if (ctx->c_split_k > 0) {
+    // split every tile's list into units of about c_split_k reduction
+    // elements
+    std::vector<int> h_tasks((size_t)npt * nqt * nslab);
+    GW_TRY(cudaMemcpy(h_tasks.data(), tasks, h_tasks.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> raster;
+    for (size_t t = 0; t < h_counts.size(); ++t)
+      if (h_counts[t] > 0) raster.push_back((int)t);
+    std::stable_sort(raster.begin(), raster.end(), [&](int a, int c) {
+      const int pa = a / nqt, qa = a % nqt, pc = c / nqt, qc = c % nqt;
+      if (pa / 8 != pc / 8) return pa / 8 < pc / 8;
+      if (qa != qc) return qa < qc;
+      return pa < pc;
+    });
+    std::vector<std::vector<std::pair<int, int>>> segs(raster.size());
+    for (size_t r = 0; r < raster.size(); ++r) {
+      const int t = raster[r];
+      const int* lst = &h_tasks[(size_t)t * nslab];
+      int i0 = 0;
+      long long kk = 0;
+      for (int i = 0; i < h_counts[t]; ++i) {
+        kk += slab_len[lst[i]];
+        if (kk >= ctx->c_split_k || i == h_counts[t] - 1) {
+          segs[r].push_back({i0, i + 1 - i0});
+          i0 = i + 1;
+          kk = 0;
+        }
+      }
+    }
+    // units in order of their first reduction index (then raster): CTAs that
+    // run side by side stream the same K window of X and Y through L2
+    struct Unit {
+      long long k0;
+      int tile, first, count;
+    };
+    std::vector<Unit> units;
+    for (size_t r = 0; r < raster.size(); ++r)
+      for (const auto& sg : segs[r])
+        units.push_back({slab_k0[h_tasks[(size_t)raster[r] * nslab + sg.first]], raster[r], sg.first,
+                         sg.second});
+    std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& c) { return a.k0 < c.k0; });
+    std::vector<int> u_tile, u_first, u_count;
+    for (const Unit& u : units) {
+      u_tile.push_back(u.tile);
+      u_first.push_back(u.first);
+      u_count.push_back(u.count);
+    }
+    int *d_ut, *d_uf, *d_uc;
+    if ((rc = upload(ctx, "unit_tile", u_tile, &d_ut))) return rc;
+    if ((rc = upload(ctx, "unit_first", u_first, &d_uf))) return rc;
+    if ((rc = upload(ctx, "unit_count", u_count, &d_uc))) return rc;
+    GW_TRY(cudaEventRecord(ec0, ctx->stream));
+    if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_ut, d_uf, d_uc,
+                                (int)u_tile.size(), tasks, counts,
+                                nslab, d_k0, d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err,
+                                ctx->stream))
+      return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+  } else {
+    int* d_active;
+    if ((rc = upload(ctx, "active_tiles", active, &d_active))) return rc;
+    GW_TRY(cudaEventRecord(ec0, ctx->stream));
+    if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_active,
+                          (int)active.size(), tasks, counts, nslab, d_k0,
+                          d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
+      return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+  }
   GW_CHECK_LAUNCH();
   GW_TRY(cudaEventRecord(ec1, ctx->stream));
   ctx->stats.c_launches += 1;
@@ -1132,13 +1234,23 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->batch_bytes = value;
     return GW_OK;
   }
+  if (!strcmp(key, "c_split_k")) {
+    if (!(value >= 0 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "c_split_k must be in [0, 2^30]");
+    ctx->c_split_k = (int)value;
+    return GW_OK;
+  }
+  if (!strcmp(key, "c_order")) {
+    if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "c_order must be 0 or 1");
+    ctx->c_order = (int)value;
+    return GW_OK;
+  }
   if (!strcmp(key, "mlp_margin")) {
     if (!std::isfinite(value)) return fail(ctx, GW_ERR_INVALID_ARG, "mlp_margin must be finite");
     ctx->mlp_margin = value;
     return GW_OK;
   }
   if (!strcmp(key, "flush_k")) {
-    if (!(value >= 64 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [64, 2^30]");
+    if (!(value >= 16 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [16, 2^30]");
     ctx->flush_k = (int)value;
     return GW_OK;
   }
@@ -1154,7 +1266,7 @@ int gw_mlp_log(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
                float* target_out, long long cap, long long* n_out) {
   if (!ctx || !n_out || cap < 0 || (cap > 0 && (!feat_out || !target_out))) return GW_ERR_INVALID_ARG;
   ctx->err.clear();
-  if (precision != GW_BF16X3 && precision != GW_BF16X6)
+  if (precision != GW_BF16X3 && precision != GW_BF16X6 && precision != GW_FP16X3)
     return fail(ctx, GW_ERR_UNSUPPORTED, "gw_mlp_log: tasks are logged on the tensor-core route");
   if (tau_count < 0 || tau_first < 0 || tau_first + tau_count > (int)ctx->tau.size())
     return fail(ctx, GW_ERR_INVALID_ARG, "gw_mlp_log: tau range out of bounds");
@@ -1195,14 +1307,15 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   if (tau_first < 0 || tau_count < 0 || tau_first + tau_count > (int)ctx->tau.size())
     return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: tau range out of bounds");
   if (!(thr >= 0.0) || !std::isfinite(thr)) return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: thr must be finite and >= 0");
-  if (precision < GW_FP64 || precision > GW_BF16X6)
+  if (precision < GW_FP64 || precision > GW_FP16X3)
     return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown precision");
   if (screening != GW_SCREEN_BOUND && screening != GW_SCREEN_MLP)
     return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: unknown screening mode");
-  const bool tc_prec = precision == GW_BF16X3 || precision == GW_BF16X6;
+  const bool tc_prec = precision == GW_BF16X3 || precision == GW_BF16X6 || precision == GW_FP16X3;
   if (screening == GW_SCREEN_MLP && !tc_prec)
     return fail(ctx, GW_ERR_UNSUPPORTED,
-                "chi_tau: learned screening acts on the tensor-core route (GW_BF16X3 / GW_BF16X6)");
+                "chi_tau: learned screening acts on the tensor-core route (GW_BF16X3 / GW_BF16X6 / "
+                "GW_FP16X3)");
   if (screening == GW_SCREEN_MLP && !ctx->mlp_ready)
     return fail(ctx, GW_ERR_ORDER, "chi_tau: learned screening needs gw_mlp_init/gw_mlp_train first");
   if (tau_count > 0 && !chi_out) return fail(ctx, GW_ERR_INVALID_ARG, "chi_tau: chi_out is null");
@@ -1215,17 +1328,18 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   int rc;
   if ((rc = build_panels(ctx, thr))) return rc;
   const bool f64 = precision == GW_FP64;
-  const bool tcpath = precision == GW_BF16X3 || precision == GW_BF16X6;
+  const bool tcpath = tc_prec;
+  const int f16 = precision == GW_FP16X3;
   if (ctx->last_precision != precision) {
     ws_release_all(ctx);
     ctx->last_precision = precision;
   }
   if (!f64 && !tcpath && (rc = ensure_panel32(ctx))) return rc;
-  if (tcpath && (rc = ensure_pt(ctx, precision == GW_BF16X6 ? 3 : 2))) return rc;
+  if (tcpath && (rc = ensure_pt(ctx, precision == GW_BF16X6 ? 3 : 2, f16))) return rc;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;
   // device bytes per operand element: FP64, FP32, or FP32 plus bf16 slices
   const size_t esz = f64 ? sizeof(double)
-                         : precision == GW_BF16X6 ? 6 : precision == GW_BF16X3 ? 4 : sizeof(float);
+                         : precision == GW_BF16X6 ? 6 : tcpath ? 4 : sizeof(float);
   std::vector<Batch> batches =
       plan_batches(ctx, esz, ctx->batch_bytes, tcpath ? gw::tc_tile_rows() : 0);
   ctx->stats.n_batches = (int)batches.size();
@@ -1260,6 +1374,23 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
                       ctx->stream);
     GW_CHECK_LAUNCH();
     ctx->stats.kernel_launches += 3;
+    if (f16) {
+      // binary16 scales of this tau: max |G| for the G slices, and the bounds
+      // |X| <= max_mu sum_lambda |G^occ| * max |T| (Y alike with G^virt)
+      double* gst;
+      double h[4];
+      if ((rc = wsT(ctx, "g_absmax", 4, &gst))) return rc;
+      gw::launch_absmax_rowsum(go, nao, nao, nao, gst, ctx->stream);
+      gw::launch_absmax_rowsum(gv, nao, nao, nao, gst + 2, ctx->stream);
+      GW_CHECK_LAUNCH();
+      ctx->stats.kernel_launches += 2;
+      GW_TRY(cudaMemcpyAsync(h, gst, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+      GW_TRY(cudaStreamSynchronize(ctx->stream));
+      ctx->tc_scale[0] = gw::pow2_scale(h[0]);
+      ctx->tc_scale[1] = gw::pow2_scale(h[2]);
+      ctx->tc_scale[2] = gw::pow2_scale(h[1] * ctx->t_absmax);
+      ctx->tc_scale[3] = gw::pow2_scale(h[3] * ctx->t_absmax);
+    }
     std::vector<unsigned char> hfo((size_t)n_at * n_at, 1), hfv((size_t)n_at * n_at, 1);
     if (thr > 0.0) {
       gw::launch_sym_block_filter(go, nao, ctx->d_ao_off, n_at, thr, flo, ctx->stream);

@@ -68,6 +68,8 @@ int build_panels_for(gw_ctx* ctx, double thr);
 // the network predicts below thr (minus the margin) from the lists.
 struct MlpBatch {
   int s0, ns, P0, prow, nslab, npt, nqt, tile, per, pa0, npa, slices;
+  int f16;           // slices in binary16 holding X / xinv and Y / yinv
+  float xinv, yinv;
   long long Kb;
   const void* xs;
   const void* ys;
@@ -110,6 +112,7 @@ struct gw_ctx {
   long long* d_blk_off = nullptr;
   double* d_blk_norm = nullptr;
   std::vector<double> blk_norm;
+  double t_absmax = 0.0;  // max |(mu sigma|P)| over the stored blocks
 
   // Green's function inputs
   bool have_greens = false;
@@ -132,9 +135,11 @@ struct gw_ctx {
 
   // transposed, split panels for the tensor-core steps A/B
   bool pt_ok = false;
-  int pt_slices = 0;
+  int pt_slices = 0, pt_f16 = 0;
   double pt_thr = -1.0;
-  void* d_pt = nullptr;           // [slices][pt_rows][pt_kmax] bf16
+  double pt_scale = 1.0;          // binary16 slices hold pt_scale * T
+  double tc_scale[4] = {1, 1, 1, 1};  // binary16 scales of G^occ, G^virt, X, Y (current tau)
+  void* d_pt = nullptr;           // [slices][pt_rows][pt_kmax] 16-bit slices
   long long pt_rows = 0;
   int pt_kmax = 0;
   std::vector<gw::PanelTaskTC> pt_tasks;  // per atom (K == 0: none)
@@ -157,8 +162,13 @@ struct gw_ctx {
   // options
   double batch_bytes = 40e9;
   int batch_atoms = 0;
-  int flush_k = 256;
-  int last_precision = -1;  // tensor-core step C: FP32 accumulator drained every flush_k elements
+  // tensor cores: main FP32 accumulator drained every flush_k reduction elements
+  int flush_k = 64;
+  int last_precision = -1;
+  int c_order = 0;   // step-C tile order: 0 longest first, 1 grouped raster
+  // step-C work units: tiles split into runs of about c_split_k reduction
+  // elements, FP64 atomics into chi (0: whole tiles, bitwise reproducible)
+  int c_split_k = 2048;
 
   gw_stats stats{};
 };

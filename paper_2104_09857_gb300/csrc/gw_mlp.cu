@@ -134,7 +134,8 @@ int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb) {
     n_tasks += c;
   }
   if (ctx->mlp_mode == 1) {
-    gw::mlp_task_norms(mb.xs, mb.ys, mb.slices, (long long)mb.prow * mb.Kb, (long long)ctx->nri * mb.Kb,
+    gw::mlp_task_norms(mb.xs, mb.ys, mb.slices, mb.f16, mb.xinv, mb.yinv, (long long)mb.prow * mb.Kb,
+                       (long long)ctx->nri * mb.Kb,
                        mb.Kb, mb.prow, ctx->nri, mb.tasks, mb.counts, mb.nslab, mb.npt, mb.nqt, max_count,
                        mb.tile, mb.slab_k0, mb.slab_len, (float*)aux.p, st);
     ML_TRY(cudaGetLastError());

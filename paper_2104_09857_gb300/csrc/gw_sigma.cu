@@ -119,12 +119,14 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
     ctx->err = "gw_sigma_tau: bad arguments";
     return GW_ERR_INVALID_ARG;
   }
-  if (precision != GW_FP64 && precision != GW_BF16X3 && precision != GW_BF16X6) {
-    ctx->err = "gw_sigma_tau: precision must be GW_FP64, GW_BF16X3 or GW_BF16X6";
+  if (precision != GW_FP64 && precision != GW_BF16X3 && precision != GW_BF16X6 &&
+      precision != GW_FP16X3) {
+    ctx->err = "gw_sigma_tau: precision must be GW_FP64, GW_BF16X3, GW_BF16X6 or GW_FP16X3";
     return GW_ERR_UNSUPPORTED;
   }
   const bool mixed = precision != GW_FP64;
   const int slices = precision == GW_BF16X6 ? 3 : 2;
+  const int f16 = precision == GW_FP16X3;
   const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at, n_tau = (int)ctx->tau.size();
   for (int a = 0; a < n_orb; ++a)
     if (orbitals[a] < 0 || orbitals[a] >= nao) {
@@ -197,7 +199,7 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
   //   z = -(y B^T)   (rows mu, columns nu, K = Q)  = B W B^T
   const int tile = gw::tc_tile_rows();
   const int kpad = (nri + 63) / 64 * 64;
-  DevBuf b_bs, b_ws, b_ys, b_tl1, b_tk1, b_ct1, b_k01, b_ln1, b_tl2, b_tk2, b_ct2, b_err;
+  DevBuf b_bs, b_ws, b_ys, b_tl1, b_tk1, b_ct1, b_k01, b_ln1, b_tl2, b_tk2, b_ct2, b_err, b_mx;
   int nslab = 0, n_tiles1 = 0, n_tiles2 = 0, nqt1 = 0, nqt2 = 0;
   CUtensorMap m_b, m_w, m_y, m_bq;
   if (mixed) {
@@ -238,10 +240,11 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
     SG_TRY(cudaMalloc(&b_ws.p, (size_t)slices * nri * kpad * 2));
     SG_TRY(cudaMalloc(&b_ys.p, (size_t)slices * nao * kpad * 2));
     SG_TRY(cudaMalloc(&b_err.p, sizeof(int)));
+    SG_TRY(cudaMalloc(&b_mx.p, 4 * sizeof(double)));
     SG_TRY(cudaMemsetAsync(b_err.p, 0, sizeof(int), st));
-    if (gw::make_slice_map(&m_b, b_bs.p, kpad, nao, slices, tile) ||
-        gw::make_slice_map(&m_w, b_ws.p, kpad, nri, slices, tile) ||
-        gw::make_slice_map(&m_y, b_ys.p, kpad, nao, slices, tile)) {
+    if (gw::make_slice_map(&m_b, b_bs.p, kpad, nao, slices, tile, f16) ||
+        gw::make_slice_map(&m_w, b_ws.p, kpad, nri, slices, tile, f16) ||
+        gw::make_slice_map(&m_y, b_ys.p, kpad, nao, slices, tile, f16)) {
       ctx->err = "gw_sigma_tau: cuTensorMapEncodeTiled failed";
       return GW_ERR_CUDA;
     }
@@ -261,19 +264,35 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
         gw::chain_dgemm(false, false, nao, nri, nri, 1.0, b, nri, wt, nri, 0.0, y, nri, st);  // Y = B W
         gw::chain_dgemm(false, true, nao, nao, nri, 1.0, y, nri, b, nri, 0.0, z, nao, st);    // Z = Y B^T
       } else {
-        gw::launch_split_f64(b, nri, nao, nri, kpad, slices, b_bs.p, st);
-        gw::launch_split_f64(wt, nri, nri, nri, kpad, slices, b_ws.p, st);
+        // binary16 scales: max |B|, max |W| and the bound |B W| <= max_mu
+        // sum_P |B[mu][P]| * max |W| (all 1 for bf16 slices)
+        double s_b = 1.0, s_w = 1.0, s_y = 1.0;
+        if (f16) {
+          double h[4];
+          gw::launch_absmax_rowsum(b, nri, nao, nri, (double*)b_mx.p, st);
+          gw::launch_absmax_rowsum(wt, nri, nri, nri, (double*)b_mx.p + 2, st);
+          SG_TRY(cudaGetLastError());
+          SG_TRY(cudaMemcpyAsync(h, b_mx.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+          SG_TRY(cudaStreamSynchronize(st));
+          s_b = gw::pow2_scale(h[0]);
+          s_w = gw::pow2_scale(h[2]);
+          s_y = gw::pow2_scale(h[1] * h[2]);
+        }
+        gw::launch_split_f64(b, nri, nao, nri, kpad, slices, f16, s_b, b_bs.p, st);
+        gw::launch_split_f64(wt, nri, nri, nri, kpad, slices, f16, s_w, b_ws.p, st);
         SG_TRY(cudaMemsetAsync(y, 0, (size_t)nao * nri * 8, st));
-        if (gw::launch_chi_tc(slices, m_b, m_w, (const int*)b_tl1.p, n_tiles1, (const int*)b_tk1.p,
+        if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_b * s_w)), m_b, m_w, (const int*)b_tl1.p,
+                              n_tiles1, (const int*)b_tk1.p,
                               (const int*)b_ct1.p, nslab, (const long long*)b_k01.p,
                               (const int*)b_ln1.p, 0, nao, nri, nqt1, y, ctx->flush_k, (int*)b_err.p, st)) {
           ctx->err = "gw_sigma_tau: tensor-core launch setup failed";
           return GW_ERR_CUDA;
         }
         // y holds -(B W); its slices are the row operand of the second product
-        gw::launch_split_f64(y, nri, nao, nri, kpad, slices, b_ys.p, st);
+        gw::launch_split_f64(y, nri, nao, nri, kpad, slices, f16, s_y, b_ys.p, st);
         SG_TRY(cudaMemsetAsync(z, 0, nn_ao * 8, st));
-        if (gw::launch_chi_tc(slices, m_y, m_bq, (const int*)b_tl2.p, n_tiles2, (const int*)b_tk2.p,
+        if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_y * s_b)), m_y, m_bq, (const int*)b_tl2.p,
+                              n_tiles2, (const int*)b_tk2.p,
                               (const int*)b_ct2.p, nslab, (const long long*)b_k01.p,
                               (const int*)b_ln1.p, 0, nao, nao, nqt2, z, ctx->flush_k, (int*)b_err.p, st)) {
           ctx->err = "gw_sigma_tau: tensor-core launch setup failed";

@@ -3,8 +3,10 @@
 // a 2-hidden-layer ReLU network with bf16 weights and FP32 accumulation
 // (forward, backward, Adam), and the compaction of task lists by prediction.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "k_mlp.h"
 
@@ -80,9 +82,15 @@ __global__ void k_task_features(const int* __restrict__ tasks, const int* __rest
 
 // log10 of the Frobenius norm of one task's contribution
 //   sum_{k in slab} X[p][k] Y[q][k]  over the tile's rows p and columns q,
-// operands rebuilt from their bf16 slices; one CTA (256 threads) per task.
-__global__ void k_task_norms(const __nv_bfloat16* __restrict__ xs, const __nv_bfloat16* __restrict__ ys,
-                             int slices, long long xslice, long long yslice, long long ldk,
+// operands rebuilt from their 16-bit slices (bf16, or binary16 holding the
+// operand times a power of two: xinv / yinv undo it); one CTA (256 threads)
+// per task.
+__device__ __forceinline__ float slice_value(uint16_t b, int f16) {
+  return f16 ? __half2float(__ushort_as_half(b)) : __bfloat162float(__ushort_as_bfloat16(b));
+}
+__global__ void k_task_norms(const uint16_t* __restrict__ xs, const uint16_t* __restrict__ ys,
+                             int slices, int f16, float xinv, float yinv, long long xslice,
+                             long long yslice, long long ldk,
                              int prow, int nri, const int* __restrict__ tasks,
                              const int* __restrict__ counts, int nslab, int nqt, int tile,
                              const long long* __restrict__ slab_k0, const int* __restrict__ slab_len,
@@ -106,10 +114,10 @@ __global__ void k_task_norms(const __nv_bfloat16* __restrict__ xs, const __nv_bf
       float va = 0.f, vb = 0.f;
       if (p < prow && kk + k < len)
         for (int s = 0; s < slices; ++s)
-          va += __bfloat162float(xs[s * xslice + static_cast<long long>(p) * ldk + k0 + kk + k]);
+          va += xinv * slice_value(xs[s * xslice + static_cast<long long>(p) * ldk + k0 + kk + k], f16);
       if (q < nri && kk + k < len)
         for (int s = 0; s < slices; ++s)
-          vb += __bfloat162float(ys[s * yslice + static_cast<long long>(q) * ldk + k0 + kk + k]);
+          vb += yinv * slice_value(ys[s * yslice + static_cast<long long>(q) * ldk + k0 + kk + k], f16);
       As[k][r] = va;
       Bs[k][r] = vb;
     }
@@ -317,14 +325,15 @@ void mlp_task_features(const int* tasks, const int* counts, int nslab, int npt, 
                                                   cent_p, cent_q, cent_c, xyz, n_ao, log_tau, feat);
 }
 
-void mlp_task_norms(const void* xs, const void* ys, int slices, long long xslice, long long yslice,
-                    long long ldk, int prow, int nri, const int* tasks, const int* counts, int nslab,
-                    int npt, int nqt, int max_count, int tile, const long long* slab_k0,
-                    const int* slab_len, float* target, cudaStream_t st) {
+void mlp_task_norms(const void* xs, const void* ys, int slices, int f16, float xinv, float yinv,
+                    long long xslice, long long yslice, long long ldk, int prow, int nri, const int* tasks,
+                    const int* counts, int nslab, int npt, int nqt, int max_count, int tile,
+                    const long long* slab_k0, const int* slab_len, float* target, cudaStream_t st) {
   if (max_count == 0) return;
   dim3 g(npt * nqt, max_count);
-  mlp::k_task_norms<<<g, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(xs),
-                                       static_cast<const __nv_bfloat16*>(ys), slices, xslice, yslice,
+  mlp::k_task_norms<<<g, 256, 0, st>>>(static_cast<const uint16_t*>(xs),
+                                       static_cast<const uint16_t*>(ys), slices, f16, xinv, yinv,
+                                       xslice, yslice,
                                        ldk, prow, nri, tasks, counts, nslab, nqt, tile, slab_k0, slab_len,
                                        target);
 }

@@ -18,10 +18,10 @@ void mlp_task_features(const int* tasks, const int* counts, int nslab, int npt, 
                        const float* xn, const float* yn, const float* cent_p, const float* cent_q,
                        const float* cent_c, const float* xyz, const int* n_ao, float log_tau,
                        float* feat, cudaStream_t st);
-void mlp_task_norms(const void* xs, const void* ys, int slices, long long xslice, long long yslice,
-                    long long ldk, int prow, int nri, const int* tasks, const int* counts, int nslab,
-                    int npt, int nqt, int max_count, int tile, const long long* slab_k0,
-                    const int* slab_len, float* target, cudaStream_t st);
+void mlp_task_norms(const void* xs, const void* ys, int slices, int f16, float xinv, float yinv,
+                    long long xslice, long long yslice, long long ldk, int prow, int nri, const int* tasks,
+                    const int* counts, int nslab, int npt, int nqt, int max_count, int tile,
+                    const long long* slab_k0, const int* slab_len, float* target, cudaStream_t st);
 void mlp_forward(const void* wb, const float* x, long long n, const int* valid, int stride, float* z1,
                  float* z2, float* y, cudaStream_t st);
 void mlp_backward(const void* wb, const float* x, const float* z1, const float* z2, const float* y,

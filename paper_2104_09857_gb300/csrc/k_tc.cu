@@ -1,9 +1,13 @@
 // Tensor-core (tcgen05) kernels of the mixed-precision chi(i tau) path.
 //
-// Split-BF16 products: every operand value x is stored as S bfloat16 slices
-// x = x_0 + x_1 + ... (x_0 = bf16(x), x_{i+1} = bf16(x - x_0 - .. - x_i)).  A
-// product a*b is formed from the slice pairs (i, j) with i + j <= S - 1:
-// S = 2 gives 3 products (a0b0 + a0b1 + a1b0), S = 3 gives 6.
+// Split products: every operand value x is stored as S 16-bit slices
+// x = x_0 + x_1 + ... (x_0 = h(x), x_{i+1} = h(x - x_0 - .. - x_i)), h the
+// rounding to bfloat16 or, for the FP16 form, to binary16 after scaling the
+// whole operand by a power of two c (slices of c x; the epilogues multiply by
+// the exact reciprocal).  A product a*b is formed from the slice pairs (i, j)
+// with i + j <= S - 1: S = 2 gives 3 products (a0b0 + a0b1 + a1b0), S = 3
+// gives 6.  With 8 significant bits per bf16 slice, S = 3 carries 24 bits;
+// with 11 per binary16 slice, S = 2 carries 22.
 //
 // One persistent, warp-specialised kernel template serves the three
 // contractions of Eq. 3.  A job supplies, per output tile, the rows of the A
@@ -17,21 +21,25 @@
 // Warp roles (320 threads):
 //   warp 0      TMA producer (one thread): A and B slices of each K step
 //   warp 1      TMEM allocator and MMA issuer (one thread)
-//   warps 2..9  epilogue: every chunk of `per_chunk` K steps the TMEM
-//               accumulators are read into an FP32 register sum per element;
-//               the job writes it out at the end of a tile (ChiJob also every
-//               kFlushChunks chunks).
-// The tensor cores' FP32 accumulation loses precision with every addition
-// into a large accumulator (the error grows linearly with their number), so
-// the main slice product (0, 0) and the small ones accumulate separately and
-// both are drained every chunk.  TMEM: 2 buffers x (main 128 + small 128)
-// columns.  Every mbarrier wait is bounded; on time-out the CTA raises the
+//   warps 2..9  epilogue: the TMEM accumulators are read into an FP32
+//               register sum per element; the job writes it out at the end
+//               of a tile (ChiJob also every kWriteK reduction elements).
+// The tensor cores' FP32 accumulation rounds each MMA step's result toward
+// zero (measured: a bias of about half an ulp per step, so the relative
+// error grows with the number of steps between drains), so the main slice
+// product (0, 0) accumulates alone and is drained every few MMA steps
+// (flush_k reduction elements); the small products, 2^-8 of it or less,
+// share a second accumulator drained every kSmallK elements.  TMEM: main
+// 2 x 128 columns, small 2 x 128 columns, each double-buffered.  Every mbarrier wait is bounded; on time-out the CTA raises the
 // error flag, waits (bounded) for the copies and products it issued, frees
 // its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cmath>
 
 #include "gw_internal.h"
 #include "k_tc.h"
@@ -46,9 +54,11 @@ constexpr int kMmaK = 16;
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiCols = kTileN / 2;
-constexpr int kFlushChunks = 8;
+constexpr int kSmallK = 2048;  // reduction elements between drains of the small accumulator
+constexpr int kWriteK = 1024;  // reduction elements between ChiJob write-outs
 constexpr int kTmemCols = 512;
-constexpr uint32_t kMaxPolls = 1u << 24;
+constexpr uint32_t kSuspendNs = 20000;            // longest suspension of one try_wait
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -64,27 +74,40 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps in hardware (up to kSuspendNs) instead of spinning on issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false on time-out or abort.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase of the given parity; false on time-out
+// (kWaitLimitNs) or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t i = 0; i < kMaxPolls; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u) {
-      if (*abort_flag) return false;
-      __nanosleep(128);
-    }
+  if (mbar_try_wait_sleep(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
   }
-  return false;
+}
+// Bounded wait without abort check (clean-up after an abort).
+__device__ __forceinline__ void mbar_wait_cleanup(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait_sleep(bar, parity) && global_ns() - t0 < kWaitLimitNs) {
+  }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
                                             uint64_t* bar) {
@@ -111,10 +134,33 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= static_cast<uint64_t>(2) << 61;
   return d;
 }
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+// Instruction descriptor of kind::f16: BF16 x BF16 (or F16 x F16) -> FP32,
+// both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_f32(int m, int n, bool f16) {
+  return (1u << 4) | (f16 ? 0u : ((1u << 7) | (1u << 10))) | (static_cast<uint32_t>(n >> 3) << 17) |
          (static_cast<uint32_t>(m >> 4) << 24);
+}
+// One slice of v (bf16, or binary16 when f16): returns its bits and leaves
+// the remainder v - slice in v (exact).
+__device__ __forceinline__ uint16_t take_slice(float& v, bool f16) {
+  if (f16) {
+    const __half h = __float2half_rn(v);
+    v -= __half2float(h);
+    return __half_as_ushort(h);
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  v -= __bfloat162float(h);
+  return __bfloat16_as_ushort(h);
+}
+__device__ __forceinline__ uint16_t take_slice(double& v, bool f16) {
+  if (f16) {
+    const __half h = __double2half(v);
+    v -= static_cast<double>(__half2float(h));
+    return __half_as_ushort(h);
+  }
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  v -= static_cast<double>(__bfloat162float(h));
+  return __bfloat16_as_ushort(h);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -130,14 +176,33 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// acc[j] += TMEM[lane row][taddr column + j], j < 64: two 32-column loads,
+// each followed by its wait (the registers pass through the wait's asm so
+// that no use of them can be scheduled before it).  The 320-thread block
+// leaves 168 registers per thread, too few for one 64-column load.
+__device__ __forceinline__ void tmem_add64(uint32_t taddr, float (&acc)[64]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + static_cast<uint32_t>(h * 32)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[h * 32 + j] += __uint_as_float(r[j]);
+  }
 }
+// Drain cadence of the persistent kernel, in MMA steps of kMmaK reduction
+// elements: the main accumulator every `main` steps, the small one every
+// `small_every` main drains; periodic jobs write out every `write_every`
+// main drains.
+struct Cadence {
+  int main, small_every, write_every;
+};
 
 // Per-epilogue-warp staging for coalesced stores: 32 rows x 34 bf16, or
 // 32 rows x 17 floats (both 2176 bytes).
@@ -157,8 +222,10 @@ struct Smem {
 // step C job
 // ---------------------------------------------------------------------------
 struct ChiJob {
-  const int* tile_list;  // active tiles, tile = pt * nqt + qt
-  int n_tiles;
+  const int* tile_list;  // work units: tile = pt * nqt + qt of unit u
+  int n_tiles;           // number of units
+  const int* unit_first; // optional (split K): first list entry and entry
+  const int* unit_count; // count of unit u; null = the tile's whole list
   const int* tasks;
   const int* counts;
   int max_slab;
@@ -166,6 +233,7 @@ struct ChiJob {
   const int* slab_len;
   int nqt, P0, prow, nri;
   double* chi;
+  float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
   static constexpr bool kPeriodic = true;
 
   struct Tile {
@@ -177,8 +245,13 @@ struct ChiJob {
     Tile T;
     T.ya = (id / nqt) * kTileM;
     T.yb = (id % nqt) * kTileN;
-    T.cnt = counts[id];
-    T.list = tasks + static_cast<long long>(id) * max_slab;
+    if (unit_first) {
+      T.cnt = unit_count[t];
+      T.list = tasks + static_cast<long long>(id) * max_slab + unit_first[t];
+    } else {
+      T.cnt = counts[id];
+      T.list = tasks + static_cast<long long>(id) * max_slab;
+    }
     return T;
   }
   __device__ long long nsteps(const Tile& T) const {
@@ -227,10 +300,30 @@ struct ChiJob {
       __syncwarp();
       const int col = lane & 15, sub = lane >> 4;
       const int q = T.yb + c0 + cc + col;
+      if (unit_first) {
+        // units of one tile may run concurrently when K is split
 #pragma unroll
-      for (int i = 0; i < 32; i += 2) {
-        const int p = T.ya + quad * 32 + i + sub;
-        if (p < prow && q < nri) chi[static_cast<long long>(P0 + p) * nri + q] -= static_cast<double>(f[(i + sub) * 17 + col]);
+        for (int i = 0; i < 32; i += 2) {
+          const int p = T.ya + quad * 32 + i + sub;
+          if (p < prow && q < nri)
+            atomicAdd(chi + static_cast<long long>(P0 + p) * nri + q,
+                      -static_cast<double>(f[(i + sub) * 17 + col] * out_scale));
+        }
+      } else {
+        // one owner per tile: all 16 loads in flight, then the stores
+        double old[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int p = T.ya + quad * 32 + 2 * i + sub;
+          old[i] = (p < prow && q < nri) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int p = T.ya + quad * 32 + 2 * i + sub;
+          if (p < prow && q < nri)
+            chi[static_cast<long long>(P0 + p) * nri + q] =
+                old[i] - static_cast<double>(f[(2 * i + sub) * 17 + col] * out_scale);
+        }
       }
       __syncwarp();
     }
@@ -240,13 +333,34 @@ struct ChiJob {
 // ---------------------------------------------------------------------------
 // steps A / B job
 // ---------------------------------------------------------------------------
+// Adds each lane's ss into norm2[key] (key < 0: nothing).  Lanes with equal
+// keys form contiguous runs; each run is summed by a segmented suffix scan
+// and its first lane issues one atomic.  Called by all 32 lanes.
+__device__ __forceinline__ void flush_norm(float ss, int key, float* norm2, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float up = __shfl_down_sync(0xffffffffu, ss, o);
+    const int kup = __shfl_down_sync(0xffffffffu, key, o);
+    if (lane + o < 32 && kup == key) ss += up;
+  }
+  const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  if (key >= 0 && (lane == 0 || kprev != key) && ss != 0.f) atomicAdd(norm2 + key, ss);
+}
+
 struct PanelJob {
-  const int4* tiles;          // (task, m-tile, n-tile, 0)
+  // mode 0 (X): A operand = transposed panel rows n = (pw, s'), B operand =
+  //   gathered G^occ rows mu; tile entry (task, PT tile, G tile).
+  // mode 1 (Y): A operand = gathered G^virt rows sigma (batch), B operand =
+  //   transposed panel rows n = (pw, mu); tile entry (task, G tile, PT tile).
+  // Either way a thread of the epilogue owns one A row, so its stores run
+  // along the contiguous index of the K layout (s, mu, s'): s' for X, the
+  // batch row sigma for Y.
+  const int4* tiles;
   int n_tiles;
   const PanelTaskTC* tasks;
-  int mode;                   // 0: X (rows mu), 1: Y (rows sigma of the batch)
-  int rows_valid;             // mode 0: n_AO; mode 1: batch AO count
-  __nv_bfloat16* out;         // slices [S][slice_elems]
+  int mode;
+  int rows_valid;             // G rows: mode 0 n_AO, mode 1 batch AO count
+  uint16_t* out;              // slices [S][slice_elems] (bf16 or binary16 bits)
   long long slice_elems, ldk;
   int P0b;
   const long long* rowbase;   // mode 1, per batch row
@@ -255,7 +369,11 @@ struct PanelJob {
   float* norm2;               // mode 0: [ns][n_at][npa], mode 1: [ns][n_at][n_at]
   const int* atom_of_ri;
   const int* atom_of_ao;
+  const int* ao_off;
   int n_at, npa, pa0, slices;
+  int f16;                    // slices in binary16 (else bf16)
+  float unscale;              // 1 / (scale of Gg x scale of PT): true Z = acc * unscale
+  float out_scale;            // scale of the Z slices
   static constexpr bool kPeriodic = false;
 
   struct Tile {
@@ -266,10 +384,15 @@ struct PanelJob {
     const PanelTaskTC& tk = tasks[e.x];
     Tile T;
     T.task = e.x;
-    T.mt = e.y;
-    T.nt = e.z;
-    T.ya = tk.g_row0 + e.y * kTileM;
-    T.yb = tk.p_row0 + e.z * kTileN;
+    T.mt = e.y;  // tile of the A operand's rows
+    T.nt = e.z;  // tile of the B operand's rows
+    if (mode == 0) {
+      T.ya = tk.p_row0 + e.y * kTileM;
+      T.yb = tk.g_row0 + e.z * kTileN;
+    } else {
+      T.ya = tk.g_row0 + e.y * kTileM;
+      T.yb = tk.p_row0 + e.z * kTileN;
+    }
     T.ksteps = tk.ksteps;
     return T;
   }
@@ -283,103 +406,93 @@ struct PanelJob {
       return v;
     }
   };
+  // The 64 register sums go through the thread's own staging row 16 at a
+  // time, so that the per-column loops stay rolled (small code).
   __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
                         uint8_t* stg) const {
     const PanelTaskTC& tk = tasks[T.task];
-    const int r = T.mt * kTileM + quad * 32 + lane;
-    const bool row_ok = r < rows_valid;
-    long long rb = 0;
-    int rm = 0, s_local = 0, m_row = 0;
-    if (row_ok) {
-      if (mode == 0) {
-        rb = tk.seg + static_cast<long long>(r) * tk.nsig;
-        s_local = tk.s_local;
-        m_row = atom_of_ao[r];
-      } else {
-        rb = rowbase[r];
-        rm = rowmul[r];
-        s_local = row_slocal[r];
-        m_row = tk.owner;
-      }
-    }
-    // Walk this row's columns n = nbase + j in 16-column groups parked in the
-    // thread's own staging row (no cross-lane traffic, so no warp sync): the
-    // squared block norms for both modes, and the Y stores of mode 1 (there
-    // consecutive rows sigma are consecutive in memory).
-    float* f = reinterpret_cast<float*>(stg) + lane * 17;
-    const int nbase = T.nt * kTileN + c0;
-    int pw = nbase / tk.nsig;
-    int sp = nbase - pw * tk.nsig;
-    int key = -1;
-    float ss = 0.f;
-    int patom = -1, patom_pw = -1;
+    const bool f = f16 != 0;
+    float* fr = reinterpret_cast<float*>(stg) + lane * 17;
+    if (mode == 0) {
+      // row n = (pw, s') of the owner's panel; columns mu = G rows
+      const int n = T.mt * kTileM + quad * 32 + lane;
+      const bool n_ok = n < tk.N;
+      const int pw = n_ok ? n / tk.nsig : 0;
+      const int sp = n - pw * tk.nsig;
+      const int patom = n_ok ? atom_of_ri[tk.p0 + pw] : 0;
+      uint16_t* o = out + static_cast<long long>(tk.p0 + pw - P0b) * ldk + tk.seg + sp;
+      const int mu0 = T.nt * kTileN + c0;
+      const int base_key = n_ok ? tk.s_local * n_at * npa + (patom - pa0) : -1;
+      int m = atom_of_ao[mu0 < rows_valid ? mu0 : rows_valid - 1];
+      int mend = ao_off[m + 1];
+      float ss = 0.f;
 #pragma unroll
-    for (int cc = 0; cc < kEpiCols; cc += 16) {
+      for (int cc = 0; cc < kEpiCols; cc += 16) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) f[j] = acc[cc + j];
-      if (row_ok) {
+        for (int j = 0; j < 16; ++j) fr[j] = acc[cc + j];
+#pragma unroll 1
         for (int j = 0; j < 16; ++j) {
-          const int n = nbase + cc + j;
-          if (n >= tk.N) break;
-          if (pw != patom_pw) {
-            patom = atom_of_ri[tk.p0 + pw];
-            patom_pw = pw;
-          }
-          const int blk = mode == 0 ? (s_local * n_at + m_row) * npa + (patom - pa0)
-                                    : (s_local * n_at + m_row) * n_at + patom;
-          float v = f[j];
-          if (blk != key) {
-            if (key >= 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
-            key = blk;
-            ss = 0.f;
-          }
+          const int mu = mu0 + cc + j;
+          if (mu >= rows_valid) break;  // warp-uniform
+          float v = fr[j] * unscale;
           ss += v * v;
-          if (mode == 1) {
-            const long long dst = static_cast<long long>(tk.p0 + pw) * ldk + rb +
-                                  static_cast<long long>(tk.aom + sp) * rm;
-            for (int s = 0; s < slices; ++s) {
-              const __nv_bfloat16 h = __float2bfloat16_rn(v);
-              out[s * slice_elems + dst] = h;
-              v -= __bfloat162float(h);
-            }
+          if (n_ok) {
+            v *= out_scale;
+            uint16_t* d = o + static_cast<long long>(mu) * tk.nsig;
+            for (int s = 0; s < slices; ++s) d[s * slice_elems] = take_slice(v, f);
           }
+          if (mu + 1 == mend || cc + j == kEpiCols - 1 || mu + 1 == rows_valid) {  // warp-uniform
+            flush_norm(ss, base_key < 0 ? -1 : base_key + m * npa, norm2, lane);
+            ss = 0.f;
+            if (mu + 1 == mend && m + 1 < n_at) mend = ao_off[++m + 1];
+          }
+        }
+      }
+    } else {
+      // row = batch AO sigma; columns n = (pw, mu') of the panel of atom tk.owner
+      const int r = T.mt * kTileM + quad * 32 + lane;
+      const bool r_ok = r < rows_valid;
+      const long long rb = r_ok ? rowbase[r] : 0;
+      const int rm = r_ok ? rowmul[r] : 0;
+      const int s_local = r_ok ? row_slocal[r] : 0;
+      const int n0 = T.nt * kTileN + c0;
+      int pw = n0 / tk.nsig;
+      int sp = n0 - pw * tk.nsig;
+      int patom = atom_of_ri[tk.p0 + (pw < tk.npw ? pw : tk.npw - 1)];
+      long long pwbase = static_cast<long long>(tk.p0 + pw) * ldk + rb;
+      const int row_key = r_ok ? (s_local * n_at + tk.owner) * n_at : -1;
+      float ss = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < kEpiCols; cc += 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) fr[j] = acc[cc + j];
+#pragma unroll 1
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + cc + j;
+          if (n >= tk.N) break;  // warp-uniform
+          float v = fr[j] * unscale;
+          ss += v * v;
+          if (r_ok) {
+            v *= out_scale;
+            uint16_t* d = out + pwbase + static_cast<long long>(tk.aom + sp) * rm;
+            for (int s = 0; s < slices; ++s) d[s * slice_elems] = take_slice(v, f);
+          }
+          const bool last = (cc + j == kEpiCols - 1) || (n + 1 == tk.N);
           if (++sp == tk.nsig) {
             sp = 0;
             ++pw;
+            pwbase += ldk;
+            const int pa = (pw < tk.npw) ? atom_of_ri[tk.p0 + pw] : -1;
+            if (pa != patom || last) {  // warp-uniform
+              flush_norm(ss, row_key < 0 ? -1 : row_key + patom, norm2, lane);
+              ss = 0.f;
+              patom = pa;
+            }
+          } else if (last) {
+            flush_norm(ss, row_key < 0 ? -1 : row_key + patom, norm2, lane);
+            ss = 0.f;
           }
         }
-      }
-    }
-    if (key >= 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
-    if (mode == 1) return;
-    // X: consecutive columns (s' of one RI function) are consecutive in
-    // memory; stage each slice through smem and store column-wise.
-    __syncwarp();
-    __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(stg);  // [32][34]
-    const int mu0 = T.mt * kTileM + quad * 32;
-#pragma unroll
-    for (int cc = 0; cc < kEpiCols; cc += 32) {
-      const int n = nbase + cc + lane;
-      const bool n_ok = n < tk.N;
-      const int cpw = n_ok ? n / tk.nsig : 0;
-      const int csp = n - cpw * tk.nsig;
-      const long long colbase = static_cast<long long>(tk.p0 + cpw - P0b) * ldk + tk.seg + csp;
-      for (int s = 0; s < slices; ++s) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const __nv_bfloat16 b = __float2bfloat16_rn(acc[cc + j]);
-          h[lane * 34 + j] = b;
-          acc[cc + j] -= __bfloat162float(b);
-        }
-        __syncwarp();
-        if (n_ok) {
-          for (int i = 0; i < 32; ++i) {
-            const int mu = mu0 + i;
-            if (mu < rows_valid)
-              out[s * slice_elems + colbase + static_cast<long long>(mu) * tk.nsig] = h[i * 34 + lane];
-          }
-        }
-        __syncwarp();
       }
     }
   }
@@ -388,13 +501,14 @@ struct PanelJob {
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <int S, class Job>
+template <int S, class Job, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_persistent(const __grid_constant__ CUtensorMap map_a,
-                    const __grid_constant__ CUtensorMap map_b, const Job job, int per_chunk,
+                    const __grid_constant__ CUtensorMap map_b, const Job job, Cadence cad,
                     int* __restrict__ err_flag) {
   using L = Smem<S>;
   constexpr int kStages = L::kStages;
+  constexpr int kSub = kStageK / kMmaK;  // MMA steps per K step
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -403,9 +517,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOperandBytes + L::kStagingBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
-  uint64_t* acc_full = bars + 2 * kStages;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* drain = acc_empty + 2;
+  uint64_t* main_full = bars + 2 * kStages;  // [2] main accumulator buffers
+  uint64_t* main_empty = main_full + 2;
+  uint64_t* small_full = main_empty + 2;     // [2] small accumulator buffers
+  uint64_t* small_empty = small_full + 2;
+  uint64_t* drain = small_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -416,8 +532,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], kEpiWarps);
+      mbar_init(&main_full[b], 1);
+      mbar_init(&main_empty[b], kEpiWarps);
+      mbar_init(&small_full[b], 1);
+      mbar_init(&small_empty[b], kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -472,70 +590,85 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 1;
         atomicOr(err_flag, 1);
         for (int s = 0; s < kStages; ++s)
-          if (armed[s])
-            for (uint32_t t = 0; t < kMaxPolls && !mbar_try_wait(&full[s], armed_parity[s]); ++t) {
-            }
+          if (armed[s]) mbar_wait_cleanup(&full[s], armed_parity[s]);
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
+    // Main product (0, 0) into a main buffer drained every cad.main MMA
+    // steps; the other products into a small buffer drained every
+    // cad.small_every main drains (their terms are 2^-8 or less of the main
+    // ones, so their accumulation error matters that much less).
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(kTileM, kTileN);
+      constexpr uint32_t idesc = idesc_f32(kTileM, kTileN, F16);
       int stage = 0;
       uint32_t phase = 0;
-      int chunk = 0;
+      int chunk = 0, schunk = 0;
       bool ok = true, issued_any = false;
       for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
-        int step = 0;
-        for (long long i = 0; i < n; ++i) {
-          const int buf = chunk & 1;
-          if (step == 0) {
-            const uint32_t use = static_cast<uint32_t>(chunk >> 1);
-            if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u, abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
+        const long long nsub = n * kSub;
+        long long js = 0;
+        int sub = 0, cin = 0;  // MMA steps into the chunk; chunks into the small chunk
+        for (long long i = 0; i < n && ok; ++i) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d_main = tmem + static_cast<uint32_t>(buf * 256);
-          const uint32_t d_small = d_main + 128u;
           const uint32_t st = smem_u32(operands + stage * L::kStageBytes);
+          const uint64_t da = desc_sw128(st), db = desc_sw128(st + S * L::kTileBytes);
 #pragma unroll
-          for (int k = 0; k < kStageK / kMmaK; ++k) {
-            const uint64_t koff = static_cast<uint64_t>((k * kMmaK * 2) >> 4);
-            const bool chunk_start = (step == 0 && k == 0);
-            mma_bf16(d_main, desc_sw128(st) + koff, desc_sw128(st + S * L::kTileBytes) + koff, idesc,
-                     chunk_start ? 0u : 1u);
-            bool first_small = true;
+          for (int k = 0; k < kSub; ++k) {
+            const int mb = chunk & 1, sb = schunk & 1;
+            if (ok && sub == 0) {
+              ok = mbar_wait(&main_empty[mb], ((static_cast<uint32_t>(chunk) >> 1) & 1u) ^ 1u,
+                             abort_flag);
+              if (ok && cin == 0)
+                ok = mbar_wait(&small_empty[sb], ((static_cast<uint32_t>(schunk) >> 1) & 1u) ^ 1u,
+                               abort_flag);
+              tc_fence_after();
+            }
+            if (ok) {
+              const uint32_t d_main = tmem + static_cast<uint32_t>(mb * 128);
+              const uint32_t d_small = tmem + 256u + static_cast<uint32_t>(sb * 128);
+              const uint64_t koff = static_cast<uint64_t>((k * kMmaK * 2) >> 4);
+              mma_bf16(d_main, da + koff, db + koff, idesc, sub == 0 ? 0u : 1u);
+              const bool fresh = (sub == 0 && cin == 0);
+              bool first_small = true;
 #pragma unroll
-            for (int a = 0; a < S; ++a) {
+              for (int a = 0; a < S; ++a) {
 #pragma unroll
-              for (int b = 0; b < S - a; ++b) {
-                if (a == 0 && b == 0) continue;
-                mma_bf16(d_small, desc_sw128(st + a * L::kTileBytes) + koff,
-                         desc_sw128(st + (S + b) * L::kTileBytes) + koff, idesc,
-                         (chunk_start && first_small) ? 0u : 1u);
-                first_small = false;
+                for (int b = 0; b < S - a; ++b) {
+                  if (a == 0 && b == 0) continue;
+                  // slice tiles are kTileBytes apart: descriptor start
+                  // addresses advance by kTileBytes >> 4
+                  constexpr uint64_t kStep = static_cast<uint64_t>(L::kTileBytes >> 4);
+                  mma_bf16(d_small, da + a * kStep + koff, db + b * kStep + koff, idesc,
+                           (fresh && first_small) ? 0u : 1u);
+                  first_small = false;
+                }
+              }
+              issued_any = true;
+              ++js;
+              if (++sub == cad.main || js == nsub) {
+                mma_commit(&main_full[mb]);
+                ++chunk;
+                sub = 0;
+                if (++cin == cad.small_every || js == nsub) {
+                  mma_commit(&small_full[sb]);
+                  ++schunk;
+                  cin = 0;
+                }
               }
             }
           }
-          issued_any = true;
+          if (!ok) break;
           mma_commit(&empty[stage]);
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
-          }
-          if (++step == per_chunk || i == n - 1) {
-            mma_commit(&acc_full[buf]);
-            ++chunk;
-            step = 0;
           }
         }
       }
@@ -544,8 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicOr(err_flag, 2);
         if (issued_any) {
           mma_commit(drain);
-          for (uint32_t t = 0; t < kMaxPolls && !mbar_try_wait(drain, 0); ++t) {
-          }
+          mbar_wait_cleanup(drain, 0);
         }
       }
     }
@@ -555,37 +687,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 2) >> 2;
     const int c0 = half * kEpiCols;
     uint8_t* stg = staging + (warp - 2) * kStgBytes;
-    const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+    const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0);
     float acc[kEpiCols];
-    int chunk = 0;
+    int chunk = 0, schunk = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
       const typename Job::Tile T = job.tile(t);
       const long long n = job.nsteps(T);
-      const long long nch = (n + per_chunk - 1) / per_chunk;
+      const long long nch = (n * kSub + cad.main - 1) / cad.main;
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
+      int cin = 0;
       for (long long c = 0; c < nch; ++c, ++chunk) {
-        const int buf = chunk & 1;
-        const uint32_t use = static_cast<uint32_t>(chunk >> 1);
-        if (!mbar_wait(&acc_full[buf], use & 1u, abort_flag)) {
+        const int mb = chunk & 1;
+        if (!mbar_wait(&main_full[mb], (static_cast<uint32_t>(chunk) >> 1) & 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-#pragma unroll
-        for (int g = 0; g < kEpiCols / 8; ++g) {
-          const uint32_t col = static_cast<uint32_t>(buf * 256 + c0 + g * 8);
-          uint32_t vm[8], vs[8];
-          tmem_ld8(row_addr + col, vm);
-          tmem_ld8(row_addr + col + 128u, vs);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[g * 8 + j] += __uint_as_float(vm[j]) + __uint_as_float(vs[j]);
-        }
+        tmem_add64(row_addr + static_cast<uint32_t>(mb * 128), acc);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        if (Job::kPeriodic && (c + 1) % kFlushChunks == 0 && c + 1 < nch) {
+        if (lane == 0) mbar_arrive(&main_empty[mb]);
+        if (++cin == cad.small_every || c + 1 == nch) {
+          const int sb = schunk & 1;
+          if (!mbar_wait(&small_full[sb], (static_cast<uint32_t>(schunk) >> 1) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          tmem_add64(row_addr + 256u + static_cast<uint32_t>(sb * 128), acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&small_empty[sb]);
+          ++schunk;
+          cin = 0;
+        }
+        if (Job::kPeriodic && (c + 1) % cad.write_every == 0 && c + 1 < nch) {
           job.write(acc, T, quad, lane, c0, stg);
 #pragma unroll
           for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
@@ -616,29 +754,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 // for r < rows_valid and k < K, zero elsewhere up to (rows, kmax).
 __global__ void k_gather_g(const double* __restrict__ g, int nao, const PanelTaskTC* __restrict__ tasks,
                            const int* __restrict__ lam, int rbase, int rows_valid, int rows_per_task,
-                           int kmax, int slices, long long slice_elems,
-                           __nv_bfloat16* __restrict__ out) {
+                           int kmax, int slices, long long slice_elems, int f16, double scale,
+                           uint16_t* __restrict__ out) {
   const PanelTaskTC tk = tasks[blockIdx.y];
   const long long n = static_cast<long long>(rows_per_task) * kmax;
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int r = static_cast<int>(i / kmax), k = static_cast<int>(i % kmax);
     double v = 0.0;
-    if (r < rows_valid && k < tk.K) v = g[static_cast<long long>(rbase + r) * nao + lam[tk.lam_off + k]];
+    if (r < rows_valid && k < tk.K)
+      v = scale * g[static_cast<long long>(rbase + r) * nao + lam[tk.lam_off + k]];
     const long long dst = static_cast<long long>(tk.g_row0 + r) * kmax + k;
-    for (int s = 0; s < slices; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      out[s * slice_elems + dst] = h;
-      v -= static_cast<double>(__bfloat162float(h));
-    }
+    for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
   }
 }
 
 // Transposed, split panel: PT[s][p_row0 + n][k] = slice s of panel[k][n]
 // (k < K, n < N; zero padding up to (npad, kmax)).  32x32 tiles via smem.
 __global__ void k_transpose_panel(const double* __restrict__ pool, const PanelTaskTC* __restrict__ tasks,
-                                  int kmax, int slices, long long slice_elems,
-                                  __nv_bfloat16* __restrict__ out) {
+                                  int kmax, int slices, long long slice_elems, int f16,
+                                  double scale, uint16_t* __restrict__ out) {
   __shared__ double tile[32][33];
   const PanelTaskTC tk = tasks[blockIdx.z];
   const int npad = (tk.N + kTileN - 1) / kTileN * kTileN;
@@ -653,20 +788,16 @@ __global__ void k_transpose_panel(const double* __restrict__ pool, const PanelTa
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int nn = n0 + i, k = k0 + tx;
-    double v = tile[tx][i];
+    double v = scale * tile[tx][i];
     const long long dst = static_cast<long long>(tk.p_row0 + nn) * kmax + k;
-    for (int s = 0; s < slices; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      out[s * slice_elems + dst] = h;
-      v -= static_cast<double>(__bfloat162float(h));
-    }
+    for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
   }
 }
 
 // Norms of the atom blocks of an operand from the accumulated squares; zero
 // the filtered ones (norm < thr, norm > 0) in every slice; flag the kept
 // nonzero blocks and the (slab, tile) pairs they touch.
-__global__ void k_slices_block_filter(__nv_bfloat16* __restrict__ Z, int slices, long long slice_elems,
+__global__ void k_slices_block_filter(uint16_t* __restrict__ Z, int slices, long long slice_elems,
                                       long long ldk, int rowoff, const int* __restrict__ ri_off,
                                       const int* __restrict__ ao_off, const int* __restrict__ n_ao,
                                       int s0, int ns, const long long* __restrict__ seg, int pa0,
@@ -696,7 +827,7 @@ __global__ void k_slices_block_filter(__nv_bfloat16* __restrict__ Z, int slices,
     for (int r = 0; r < nrows; ++r)
       for (int c = lane; c < ncols; c += 32)
         for (int sc = 0; sc < slices; ++sc)
-          Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = __float2bfloat16_rn(0.f);
+          Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = 0;  // +0 in both formats
   }
   if (nz) {
     const int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
@@ -706,34 +837,69 @@ __global__ void k_slices_block_filter(__nv_bfloat16* __restrict__ Z, int slices,
   }
 }
 
-// FP64 [rows][cols] (row stride ld) -> bf16 slices [S][rows][kpad], zero for
-// k >= cols
+// FP64 [rows][cols] (row stride ld), times scale -> 16-bit slices
+// [S][rows][kpad], zero for k >= cols
 __global__ void k_split_f64(const double* __restrict__ a, long long ld, int rows, int cols, int kpad,
-                            int slices, __nv_bfloat16* __restrict__ out) {
+                            int slices, int f16, double scale, uint16_t* __restrict__ out) {
   const long long n = static_cast<long long>(rows) * kpad;
   const long long slice = n;
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int r = static_cast<int>(i / kpad), k = static_cast<int>(i % kpad);
-    double v = k < cols ? a[static_cast<long long>(r) * ld + k] : 0.0;
-    for (int s = 0; s < slices; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      out[s * slice + i] = h;
-      v -= static_cast<double>(__bfloat162float(h));
+    double v = k < cols ? scale * a[static_cast<long long>(r) * ld + k] : 0.0;
+    for (int s = 0; s < slices; ++s) out[s * slice + i] = take_slice(v, f16 != 0);
+  }
+}
+
+// out[0] = max |a|, out[1] = max over rows of sum |a[r][:]| (out zeroed by
+// the caller): non-negative doubles order like their bit patterns.
+__global__ void k_absmax_rowsum(const double* __restrict__ a, long long ld, int rows, int cols,
+                                unsigned long long* __restrict__ out) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  double mx = 0.0, rs_max = 0.0;
+  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + warp; r < rows;
+       r += static_cast<long long>(gridDim.x) * (blockDim.x / 32)) {
+    double rs = 0.0;
+    for (int c = lane; c < cols; c += 32) {
+      const double v = fabs(a[r * ld + c]);
+      rs += v;
+      mx = fmax(mx, v);
     }
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    rs_max = fmax(rs_max, rs);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(mx)));
+    atomicMax(out + 1, static_cast<unsigned long long>(__double_as_longlong(rs_max)));
   }
 }
 
 }  // namespace tc
 
+void launch_absmax_rowsum(const double* a, long long ld, int rows, int cols, double* out2,
+                          cudaStream_t st) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+  if (rows <= 0 || cols <= 0) return;
+  int blocks = (rows + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  tc::k_absmax_rowsum<<<blocks, 256, 0, st>>>(a, ld, rows, cols, reinterpret_cast<unsigned long long*>(out2));
+}
+
+double pow2_scale(double bound) {
+  if (!(bound > 0.0) || !std::isfinite(bound)) return 1.0;
+  // the scaled bound is at most 2^14: four times below the binary16 maximum
+  return std::ldexp(1.0, 14 - static_cast<int>(std::ceil(std::log2(bound))));
+}
+
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
-                      void* out, cudaStream_t st) {
+                      int f16, double scale, void* out, cudaStream_t st) {
   const long long n = static_cast<long long>(rows) * kpad;
   if (n == 0) return;
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  tc::k_split_f64<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a, ld, rows, cols, kpad, slices,
-                                                                static_cast<__nv_bfloat16*>(out));
+  tc::k_split_f64<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a, ld, rows, cols, kpad, slices, f16,
+                                                                scale, static_cast<uint16_t*>(out));
 }
 
 // ---------------------------------------------------------------------------
@@ -768,26 +934,44 @@ int num_sms() {
   return n;
 }
 
-template <int S, class Job>
-int launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, const Job& job, int per_chunk,
-                      int* err_flag, cudaStream_t st) {
+template <int S, class Job, bool F16>
+int launch_persistent_t(const CUtensorMap& ma, const CUtensorMap& mb, const Job& job, tc::Cadence cad,
+                        int* err_flag, cudaStream_t st) {
   if (job.n_tiles == 0) return 0;
   constexpr int smem = tc::Smem<S>::kTotal;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(tc::k_tc_persistent<S, Job>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(tc::k_tc_persistent<S, Job, F16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
     attr = true;
   }
   const int grid = job.n_tiles < num_sms() ? job.n_tiles : num_sms();
-  tc::k_tc_persistent<S, Job><<<grid, tc::kThreads, smem, st>>>(ma, mb, job, per_chunk, err_flag);
+  tc::k_tc_persistent<S, Job, F16><<<grid, tc::kThreads, smem, st>>>(ma, mb, job, cad, err_flag);
   return 0;
+}
+// slices 2 or 3 in bf16, or 2 in binary16; flush_k = reduction elements
+// between drains of the main accumulator (rounded down to a multiple of 16)
+template <class Job>
+int launch_persistent(int slices, int f16, const CUtensorMap& ma, const CUtensorMap& mb, const Job& job,
+                      int flush_k, int* err_flag, cudaStream_t st) {
+  tc::Cadence cad;
+  cad.main = flush_k / tc::kMmaK > 0 ? flush_k / tc::kMmaK : 1;
+  const int fk = cad.main * tc::kMmaK;
+  cad.small_every = tc::kSmallK / fk > 0 ? tc::kSmallK / fk : 1;
+  cad.write_every = tc::kWriteK / fk > 0 ? tc::kWriteK / fk : 1;
+  if (f16) {
+    if (slices == 2) return launch_persistent_t<2, Job, true>(ma, mb, job, cad, err_flag, st);
+    return -4;
+  }
+  if (slices == 2) return launch_persistent_t<2, Job, false>(ma, mb, job, cad, err_flag, st);
+  if (slices == 3) return launch_persistent_t<3, Job, false>(ma, mb, job, cad, err_flag, st);
+  return -4;
 }
 }  // namespace
 
 int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long long rows, int slices,
-                   int box_rows) {
+                   int box_rows, int f16) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return -1;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (k_len * 2) % 16 != 0) return -2;
@@ -797,7 +981,8 @@ int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long lon
                            static_cast<cuuint64_t>(k_len * 2 * rows)};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(tc::kStageK), static_cast<cuuint32_t>(box_rows), 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+  CUresult r = fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                  const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;
@@ -805,52 +990,60 @@ int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long lon
 
 int tc_tile_rows() { return tc::kTileM; }
 
-int launch_chi_tc(int slices, const CUtensorMap& mx, const CUtensorMap& my, const int* tile_list,
-                  int n_tiles, const int* tasks, const int* counts, int max_slab,
+int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, const CUtensorMap& my,
+                  const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,
                   const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
                   double* chi, int flush_k, int* err_flag, cudaStream_t st) {
-  tc::ChiJob job{tile_list, n_tiles, tasks, counts, max_slab, slab_k0, slab_len, nqt, P0, prow, nri, chi};
-  const int per_chunk = flush_k / tc::kStageK > 0 ? flush_k / tc::kStageK : 1;
-  if (slices == 2) return launch_persistent<2>(mx, my, job, per_chunk, err_flag, st);
-  if (slices == 3) return launch_persistent<3>(mx, my, job, per_chunk, err_flag, st);
-  return -4;
+  tc::ChiJob job{tile_list, n_tiles, nullptr, nullptr, tasks, counts, max_slab, slab_k0, slab_len, nqt,
+                 P0, prow, nri, chi, out_scale};
+  return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
-int launch_panel_tc(int slices, const CUtensorMap& mg, const CUtensorMap& mp, const int4* tiles,
-                    int n_tiles, const PanelTaskTC* tasks, int mode, int rows_valid, void* out,
-                    long long slice_elems, long long ldk, int P0b, const long long* rowbase,
-                    const int* rowmul, const int* row_slocal, float* norm2, const int* atom_of_ri,
-                    const int* atom_of_ao, int n_at, int npa, int pa0, int flush_k, int* err_flag,
-                    cudaStream_t st) {
-  tc::PanelJob job{tiles, n_tiles, tasks, mode, rows_valid, static_cast<__nv_bfloat16*>(out),
-                   slice_elems, ldk, P0b, rowbase, rowmul, row_slocal, norm2, atom_of_ri,
-                   atom_of_ao, n_at, npa, pa0, slices};
-  const int per_chunk = flush_k / tc::kStageK > 0 ? flush_k / tc::kStageK : 1;
-  if (slices == 2) return launch_persistent<2>(mg, mp, job, per_chunk, err_flag, st);
-  if (slices == 3) return launch_persistent<3>(mg, mp, job, per_chunk, err_flag, st);
-  return -4;
+int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap& mx,
+                        const CUtensorMap& my, const int* unit_tile, const int* unit_first,
+                        const int* unit_count, int n_units, const int* tasks, const int* counts,
+                        int max_slab, const long long* slab_k0, const int* slab_len, int P0, int prow,
+                        int nri, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st) {
+  tc::ChiJob job{unit_tile, n_units, unit_first, unit_count, tasks, counts, max_slab, slab_k0, slab_len,
+                 nqt, P0, prow, nri, chi, out_scale};
+  return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
+}
+
+int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const CUtensorMap& mg,
+                    const CUtensorMap& mp, const int4* tiles, int n_tiles, const PanelTaskTC* tasks,
+                    int mode, int rows_valid, void* out, long long slice_elems, long long ldk, int P0b,
+                    const long long* rowbase, const int* rowmul, const int* row_slocal, float* norm2,
+                    const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
+                    int pa0, int flush_k, int* err_flag, cudaStream_t st) {
+  tc::PanelJob job{tiles, n_tiles, tasks, mode, rows_valid, static_cast<uint16_t*>(out), slice_elems,
+                   ldk, P0b, rowbase, rowmul, row_slocal, norm2, atom_of_ri, atom_of_ao, ao_off, n_at,
+                   npa, pa0, slices, f16, unscale, out_scale};
+  // mode 0: the panel rows are the A operand
+  if (mode == 0) return launch_persistent(slices, f16, mp, mg, job, flush_k, err_flag, st);
+  return launch_persistent(slices, f16, mg, mp, job, flush_k, err_flag, st);
 }
 
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
                      int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
-                     long long slice_elems, void* out, cudaStream_t st) {
+                     long long slice_elems, int f16, double scale, void* out, cudaStream_t st) {
   if (ntasks == 0) return;
   long long per = static_cast<long long>(rows_per_task) * kmax;
   int bx = static_cast<int>((per + 255) / 256);
   if (bx > 1024) bx = 1024;
   dim3 grid(bx, ntasks);
   tc::k_gather_g<<<grid, 256, 0, st>>>(g, nao, tasks, lam, rbase, rows_valid, rows_per_task, kmax,
-                                       slices, slice_elems, static_cast<__nv_bfloat16*>(out));
+                                       slices, slice_elems, f16, scale, static_cast<uint16_t*>(out));
 }
 
 void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
-                             int kmax, int slices, long long slice_elems, void* out, cudaStream_t st) {
+                             int kmax, int slices, long long slice_elems, int f16, double scale,
+                             void* out, cudaStream_t st) {
   if (ntasks == 0) return;
   for (int z0 = 0; z0 < ntasks; z0 += 65535) {
     const int nz = ntasks - z0 < 65535 ? ntasks - z0 : 65535;
     dim3 grid((max_npad + 31) / 32, (kmax + 31) / 32, nz);
-    tc::k_transpose_panel<<<grid, 256, 0, st>>>(pool, tasks + z0, kmax, slices, slice_elems,
-                                                static_cast<__nv_bfloat16*>(out));
+    tc::k_transpose_panel<<<grid, 256, 0, st>>>(pool, tasks + z0, kmax, slices, slice_elems, f16, scale,
+                                                static_cast<uint16_t*>(out));
   }
 }
 
@@ -862,7 +1055,7 @@ void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long
   const long long nblk = static_cast<long long>(ns) * n_at * npa;
   if (nblk == 0) return;
   tc::k_slices_block_filter<<<static_cast<unsigned>((nblk + 7) / 8), 256, 0, st>>>(
-      static_cast<__nv_bfloat16*>(Z), slices, slice_elems, ldk, rowoff, ri_off, ao_off, n_ao, s0, ns,
+      static_cast<uint16_t*>(Z), slices, slice_elems, ldk, rowoff, ri_off, ao_off, n_ao, s0, ns,
       seg, pa0, npa, n_at, thr, naop, norm2, blockflag, tileflag, ntile, tile_rows);
 }
 

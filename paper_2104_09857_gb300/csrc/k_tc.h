@@ -1,4 +1,10 @@
 // Launchers of the tensor-core kernels (k_tc.cu).
+//
+// Operands are 16-bit slices (bf16, or binary16 when f16 != 0) stored
+// [slices][rows][k] with k contiguous.  Binary16 slices hold the operand
+// times a power of two (pow2_scale of a bound on its magnitude); the
+// launchers take the scale of what they write and the reciprocal of the
+// product of the input scales, both exact powers of two.
 #pragma once
 
 #include <cuda.h>
@@ -8,37 +14,57 @@
 
 namespace gw {
 
-// 3D TMA map over bf16 slices stored [slices][rows][k_len] (k contiguous);
+// 3D TMA map over 16-bit slices stored [slices][rows][k_len] (k contiguous);
 // box = 64 k x box_rows rows x 1 slice, 128-byte swizzle.  0 on success.
 int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long long rows, int slices,
-                   int box_rows);
+                   int box_rows, int f16);
 // Rows (and columns) of one step-C tile of the tensor-core kernel.
 int tc_tile_rows();
-// Step C on the tensor cores: chi[P0 + p][q] -= sum over the tile's slabs of
-// X[p][k] Y[q][k], split-BF16 with `slices` slices; one CTA per entry of
-// tile_list (tile = pt * nqt + qt, 128 x 128).  err_flag != 0 after the
-// kernel means a bounded wait gave up.  Returns 0 or a negative setup error.
-int launch_chi_tc(int slices, const CUtensorMap& mx, const CUtensorMap& my, const int* tile_list,
-                  int n_tiles, const int* tasks, const int* counts, int max_slab,
+// 2^(14 - ceil(log2 bound)): scales a value of magnitude <= bound to <= 2^14
+// (1 for a zero or non-finite bound).
+double pow2_scale(double bound);
+// out2[0] = max |a|, out2[1] = max_r sum_c |a[r][c]| of an FP64 [rows][cols]
+// matrix (row stride ld), on the stream.
+void launch_absmax_rowsum(const double* a, long long ld, int rows, int cols, double* out2,
+                          cudaStream_t st);
+// Step C on the tensor cores: chi[P0 + p][q] -= out_scale * sum over the
+// tile's slabs of X[p][k] Y[q][k] with `slices` slices; one work item per
+// entry of tile_list (tile = pt * nqt + qt, 128 x 128).  err_flag != 0 after
+// the kernel means a bounded wait gave up.  Returns 0 or a negative setup
+// error (-4: unsupported slice count / format).
+int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, const CUtensorMap& my,
+                  const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,
                   const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
                   double* chi, int flush_k, int* err_flag, cudaStream_t st);
+// Step C over work units that split tiles along K: unit u computes tile
+// unit_tile[u] over list entries [unit_first[u], unit_first[u] + unit_count[u])
+// of that tile's task list and adds into chi with FP64 atomics.
+int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap& mx,
+                        const CUtensorMap& my, const int* unit_tile, const int* unit_first,
+                        const int* unit_count, int n_units, const int* tasks, const int* counts,
+                        int max_slab, const long long* slab_k0, const int* slab_len, int P0, int prow,
+                        int nri, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st);
 // Steps A/B on the tensor cores (PanelJob in k_tc.cu): mode 0 writes X, mode
-// 1 writes Y, as bf16 slices, and accumulates squared atom-block norms.
-int launch_panel_tc(int slices, const CUtensorMap& mg, const CUtensorMap& mp, const int4* tiles,
-                    int n_tiles, const PanelTaskTC* tasks, int mode, int rows_valid, void* out,
-                    long long slice_elems, long long ldk, int P0b, const long long* rowbase,
-                    const int* rowmul, const int* row_slocal, float* norm2, const int* atom_of_ri,
-                    const int* atom_of_ao, int n_at, int npa, int pa0, int flush_k, int* err_flag,
-                    cudaStream_t st);
-// FP64 [rows][cols] (row stride ld) -> `slices` bf16 slices [S][rows][kpad],
+// 1 writes Y, as slices of out_scale * (unscale * accumulator), and
+// accumulates the squared atom-block norms of unscale * accumulator.  Tile
+// entries (task, i, j): mode 0 i = panel-row tile, j = G-row tile; mode 1
+// i = G-row tile, j = panel-row tile.
+int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const CUtensorMap& mg,
+                    const CUtensorMap& mp, const int4* tiles, int n_tiles, const PanelTaskTC* tasks,
+                    int mode, int rows_valid, void* out, long long slice_elems, long long ldk, int P0b,
+                    const long long* rowbase, const int* rowmul, const int* row_slocal, float* norm2,
+                    const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
+                    int pa0, int flush_k, int* err_flag, cudaStream_t st);
+// scale * FP64 [rows][cols] (row stride ld) -> `slices` slices [S][rows][kpad],
 // zero-padded in k.
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
-                      void* out, cudaStream_t st);
+                      int f16, double scale, void* out, cudaStream_t st);
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
                      int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
-                     long long slice_elems, void* out, cudaStream_t st);
+                     long long slice_elems, int f16, double scale, void* out, cudaStream_t st);
 void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
-                             int kmax, int slices, long long slice_elems, void* out, cudaStream_t st);
+                             int kmax, int slices, long long slice_elems, int f16, double scale,
+                             void* out, cudaStream_t st);
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
                                 const int* ri_off, const int* ao_off, const int* n_ao, int s0,
                                 int ns, const long long* seg, int pa0, int npa, int n_at,

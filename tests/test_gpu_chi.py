@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 from oracle import chi as oc  # noqa: E402
 from synth import make_case  # noqa: E402
 
-TOL = {"fp64": 1e-10, "fp32": 1e-6, "bf16x6": 1e-6}
+TOL = {"fp64": 1e-10, "fp32": 1e-6, "bf16x6": 1e-6, "fp16x3": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -221,9 +221,50 @@ def test_bf16x6_many_batches_ragged_tiles_and_flush(lib):
     for atoms, flush in ((1, 64), (5, 128), (0, 256)):
         got, _ = _run(lib, case, precision="bf16x6", options={"batch_atoms": atoms, "flush_k": flush})
         _check(got, ref, TOL["bf16x6"])
-    e_short = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 64})[0], ref)
-    e_long = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 4096})[0], ref)
+    whole = {"c_split_k": 0}  # whole tiles, so that a 4096 drain interval is reached
+    e_short = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 64, **whole})[0], ref)
+    e_long = _rel_err(_run(lib, case, precision="bf16x6", options={"flush_k": 4096, **whole})[0], ref)
     assert e_long > e_short
+
+
+def test_bf16x6_split_k_units(lib):
+    """Step C over work units that split tiles along the reduction (FP64
+    atomic adds into chi): every split, from one slab per unit to whole
+    tiles, meets the bar; whole tiles are bitwise reproducible."""
+    case = make_case("ribbon28", n_tau=2)
+    ref = oc.chi_dense(case)
+    for split in (0, 1, 700, 2048, 1 << 20):
+        got, _ = _run(lib, case, precision="bf16x6", options={"c_split_k": split, "batch_atoms": 4})
+        _check(got, ref, TOL["bf16x6"])
+    a = _run(lib, case, precision="bf16x6", options={"c_split_k": 0})[0]
+    b = _run(lib, case, precision="bf16x6", options={"c_split_k": 0})[0]
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name,thr", [("benzene", 0.0), ("ribbon28", 1e-9), ("ribbon28", 1e-3)])
+def test_fp16x3_matches_oracle(lib, name, thr):
+    """Two binary16 slices of power-of-two scaled operands, 3 products."""
+    case = make_case(name, n_tau=4)
+    got, st = _run(lib, case, precision="fp16x3", thr=thr)
+    ref = oc.chi_dense(case, thr=thr)
+    _check(got, ref, TOL["fp16x3"])
+    assert st["c_launches"] > 0
+
+
+@pytest.mark.parametrize("factor", [1e-7, 1e7])
+def test_fp16x3_scaling_covers_tensor_magnitude(lib, factor):
+    """A tensor scaled by 1e-7 or 1e7 lies far outside the binary16 range
+    unscaled (chi scales by factor^2); the power-of-two operand scales keep
+    the result within the bar, whole tiles or split units alike."""
+    import dataclasses
+
+    base = make_case("ribbon28", n_tau=2)
+    t3 = dataclasses.replace(base.t3c, data=base.t3c.data * factor)
+    case = dataclasses.replace(base, t3c=t3, thr=base.thr * factor)
+    ref = oc.chi_dense(case)
+    for split in (0, 2048):
+        got, _ = _run(lib, case, precision="fp16x3", options={"c_split_k": split})
+        _check(got, ref, TOL["fp16x3"])
 
 
 def test_bf16x3_error_is_split_limited(lib):

@@ -48,13 +48,14 @@ def _compare(got_blocks, ref_blocks, tol):
     return rel
 
 
-@pytest.mark.parametrize("tau_index", [3, 19])
-def test_bf16x6_full_size_sampled_blocks(setup, tau_index):
+@pytest.mark.parametrize("precision,tau_index", [("bf16x6", 3), ("bf16x6", 19), ("fp16x3", 3),
+                                                 ("fp16x3", 19)])
+def test_mixed_full_size_sampled_blocks(setup, precision, tau_index):
     pkg, case, bo = setup
     ri = oc.offsets(case.system.n_ri)
     with pkg.Context(0) as ctx:
         ctx.load_case(case)
-        chi = ctx.chi_tau(case.thr, "bf16x6", tau_index, 1)[0]
+        chi = ctx.chi_tau(case.thr, precision, tau_index, 1)[0]
         got = [b.cpu().numpy() for b in _blocks(chi, ri, PAIRS)]
         # exact mirror across atom blocks
         p, q = PAIRS[5]

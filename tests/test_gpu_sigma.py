@@ -61,17 +61,19 @@ def test_chi_w_sigma_chain_on_device(pkg):
     assert np.abs(got - s_ref).max() <= 1e-9 * np.abs(s_ref).max()
 
 
-@pytest.mark.parametrize("name", ["benzene", "ribbon28"])
-def test_sigma_bf16x6_matches_oracle(pkg, name):
-    """The two products of Eq. 10 on the tensor cores (split bf16, 6 products):
-    within the 1e-6 mixed-precision bar of the oracle."""
+@pytest.mark.parametrize("name,precision", [("benzene", "bf16x6"), ("ribbon28", "bf16x6"),
+                                            ("benzene", "fp16x3"), ("ribbon28", "fp16x3")])
+def test_sigma_mixed_matches_oracle(pkg, name, precision):
+    """The two products of Eq. 10 on the tensor cores (split bf16, 6 products,
+    or scaled binary16, 3 products): within the 1e-6 mixed-precision bar of
+    the oracle."""
     case = make_case(name, n_tau=3)
     w = synthetic_w(case.system.nri_total, case.tau, 9)
     orbs = [case.n_occ - 1, case.n_occ]
     ref = osg.sigma_dense(case, w, orbs, thr=case.thr)
     with pkg.Context(0) as ctx:
         ctx.load_case(case)
-        got = ctx.sigma_tau(w, orbs, case.thr, precision="bf16x6")
+        got = ctx.sigma_tau(w, orbs, case.thr, precision=precision)
         fp64 = ctx.sigma_tau(w, orbs, case.thr, precision="fp64")
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-6 * scale
@@ -81,7 +83,7 @@ def test_sigma_bf16x6_matches_oracle(pkg, name):
 def test_uneven_molecule_set_mixed_and_fp64(pkg):
     """Self-energy (HOMO, LUMO) of molecules of uneven size drawn like the
     batched self-energy workload (rings and ribbon segments, 10-150 atoms,
-    thr 1e-9): per-molecule error of BF16x6 and FP64 against the block oracle
+    thr 1e-9): per-molecule error of BF16x6, FP16x3 and FP64 against the block oracle
     on three of the twenty tau points."""
     from synth import case_from_system, molecule_set
 
@@ -98,11 +100,14 @@ def test_uneven_molecule_set_mixed_and_fp64(pkg):
         with pkg.Context(0) as ctx:
             ctx.load_case(case)
             mixed = ctx.sigma_tau(w, orbs, case.thr, precision="bf16x6")[:, taus]
+            half = ctx.sigma_tau(w, orbs, case.thr, precision="fp16x3")[:, taus]
             fp64 = ctx.sigma_tau(w, orbs, case.thr, precision="fp64")[:, taus]
         scale = np.abs(ref).max()
         e_mixed = np.abs(mixed - ref).max() / scale
+        e_half = np.abs(half - ref).max() / scale
         e_fp64 = np.abs(fp64 - ref).max() / scale
         print(f"{case.system.name}: {case.system.n_atoms} atoms, bf16x6 err {e_mixed:.2e}, "
-              f"fp64 err {e_fp64:.2e}")
+              f"fp16x3 err {e_half:.2e}, fp64 err {e_fp64:.2e}")
         assert e_mixed <= 1e-6
+        assert e_half <= 1e-6
         assert e_fp64 <= 1e-10

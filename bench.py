@@ -7,7 +7,8 @@ threshold 1e-9), seeded synthetic inputs (synth).  One step = chi(i tau_j) for
 one tau point through the C ABI (steps cycle through the tau grid); inputs
 (3c tensor 11 GB, orbitals) are resident in HBM before the timed region.
 
-value  = useful TFLOP/s of the mixed-precision form (flops of the surviving
+value  = useful TFLOP/s of the mixed-precision form (default FP16x3: two scaled
+         binary16 slices, 3 tensor-core products; flops of the surviving
          atom-block products of Eq. 3's steps A, B, C; split products,
          padding and skipped work not counted), whole job.
 Also reported: ms per tau point, the FP64 form on a subset of tau points,
@@ -33,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "ribbon300"
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 lanes x 2 flop x max SM clock
-N_PRODUCTS = {"fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp64": 1}
+N_PRODUCTS = {"fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3, "fp64": 1}
+SPLIT_FORMS = ("bf16x3", "bf16x6", "fp16x3")
 
 
 def _peaks():
@@ -122,6 +124,7 @@ def cpu_oracle_sample(case, steps: int, useful_flops_per_tau: float):
     j = len(case.tau) // 2
     bo.greens(j)
     t_m, t_n, t_b = [], [], []
+    blocks = {}
     for i in range(max(1, steps)):
         p = (n_at // 2 + 37 * i) % n_at
         t0 = time.perf_counter()
@@ -130,7 +133,7 @@ def cpu_oracle_sample(case, steps: int, useful_flops_per_tau: float):
         n = bo.n_slice(j, p)
         t2 = time.perf_counter()
         cache = {("m", j, p): m, ("n", j, p): n}
-        bo.block(j, p, p, cache)
+        blocks[p] = bo.block(j, p, p, cache)
         t3 = time.perf_counter()
         t_m.append(t1 - t0)
         t_n.append(t2 - t1)
@@ -150,6 +153,8 @@ def cpu_oracle_sample(case, steps: int, useful_flops_per_tau: float):
                    f"(mean {tm:.2f} s, {tn:.2f} s, {tb:.3f} s), scaled to one tau point by "
                    f"{n_at} M + {n_at} N slices and {n_at * (n_at + 1) // 2} blocks"),
         "sample_seconds": sum(t_m) + sum(t_n) + sum(t_b),
+        "tau_index": j,
+        "blocks": blocks,
     }
 
 
@@ -257,7 +262,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0.record(stream)
     agg = {"flops_useful": 0.0, "flops_c": 0.0, "ms_step_c_kernel": 0.0, "kernel_launches": 0,
-           "flops_issued": 0.0, "c_launches": 0}
+           "flops_issued": 0.0, "c_launches": 0, "ms_step_ab": 0.0, "ms_greens": 0.0}
     for i in range(args.steps):
         st = step((i * world + rank) % n_tau, prec)
         for k in agg:
@@ -285,11 +290,13 @@ def run_ours(args):
     # roofline of the step-C kernel (the dominant kernel)
     c_time = agg["ms_step_c_kernel"] / 1e3
     achieved = agg["flops_c"] / c_time / 1e12 if c_time > 0 else None
-    if prec in ("bf16x3", "bf16x6"):
+    if prec in SPLIT_FORMS:
+        # binary16 and bf16 share the dense tensor rate (kind::f16)
         peak = peaks["bf16_tflops_sustained"] / N_PRODUCTS[prec]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "peak_note": f"{peak_src} bf16 sustained / {N_PRODUCTS[prec]} products per useful product"}
+                "peak_note": f"{peak_src} bf16 sustained (= f16 rate) / {N_PRODUCTS[prec]} "
+                             f"products per useful product"}
     else:
         peak = FFMA_PEAK_TFLOPS if prec == "fp32" else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -302,13 +309,16 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_job * 1e3 / max(1, args.steps),
         "ms_per_tau": ms_per_tau, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6",
-                                       "fp64": "f64"}[prec],
+                                       "fp16x3": "f16x3", "fp64": "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": "armchair-ribbon-298 (200 C + 98 H, 3090 AO / 7176 RI, "
                                "20 tau in [0.01, 50] a.u., thr 1e-9)",
                    "form": prec, "l2": "inputs and per-step operands larger than L2 (11 GB 3c)",
                    "parallelism": f"tau-sharded replicas x{world}"},
         "roofline": roof,
+        "step_ms": {"greens": agg["ms_greens"] / max(1, args.steps),
+                    "ab_kernels": agg["ms_step_ab"] / max(1, args.steps),
+                    "c_kernel": agg["ms_step_c_kernel"] / max(1, args.steps)},
         "gpu_launches": int(agg["kernel_launches"]),
         "clocks": clk,
     }
@@ -355,11 +365,29 @@ def run_ours(args):
                                                        case.tau.nbytes),
                              "d2h_bytes_per_step": int(nri * nri * 8),
                              "ms_per_step": t_e * 1e3 / args.e2e_steps}
-        # CPU oracle, bounded sample
+        # CPU oracle, bounded sample; its diagonal chi blocks also give a
+        # sampled error of the timed form at that tau point
         if args.cpu_samples > 0:
             per_tau = flops_job / max(1, args.steps * world)
-            result["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(
-                case, args.cpu_samples, per_tau).items() if k != "sample_seconds"}
+            res = cpu_oracle_sample(case, args.cpu_samples, per_tau)
+            result["cpu_baseline"] = {k: v for k, v in res.items()
+                                      if k not in ("sample_seconds", "tau_index", "blocks")}
+            step(res["tau_index"], prec)
+            torch.cuda.synchronize()
+            ri = np.concatenate([[0], np.cumsum(case.system.n_ri)])
+            num = den = 0.0
+            emax = rmax = 0.0
+            for p, ref in res["blocks"].items():
+                got = out[0, ri[p]:ri[p + 1], ri[p]:ri[p + 1]].cpu().numpy()
+                num += float(np.sum((got - ref) ** 2))
+                den += float(np.sum(ref ** 2))
+                emax = max(emax, float(np.abs(got - ref).max()))
+                rmax = max(rmax, float(np.abs(ref).max()))
+            result["parity"] = {"form": prec, "tau_index": res["tau_index"],
+                                "blocks": [[int(p), int(p)] for p in res["blocks"]],
+                                "rel_frobenius": (num / den) ** 0.5 if den > 0 else None,
+                                "rel_element": emax / rmax if rmax > 0 else None,
+                                "reference": "numpy FP64 block oracle"}
         result["setup"] = {"generate_s": t_gen}
     ctx.close()
     if rank == 0:
@@ -374,7 +402,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3", "bf16x6", "fp64"], default="bf16x6")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "bf16x6", "fp16x3", "fp64"],
+                    default="fp16x3")
     ap.add_argument("--fp64-taus", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=1)

@@ -29,8 +29,9 @@
 // error grows with the number of steps between drains), so the main slice
 // product (0, 0) accumulates alone and is drained every few MMA steps
 // (flush_k reduction elements); the small products, 2^-8 of it or less,
-// share a second accumulator drained every kSmallK elements.  TMEM: main
-// 2 x 128 columns, small 2 x 128 columns, each double-buffered.  Every mbarrier wait is bounded; on time-out the CTA raises the
+// share a second accumulator drained every kSmallK elements.  TMEM: three
+// main accumulators of 128 columns (the MMA may run two drains ahead of the
+// epilogue) and one small accumulator of 128 columns.  Every mbarrier wait is bounded; on time-out the CTA raises the
 // error flag, waits (bounded) for the copies and products it issued, frees
 // its TMEM and returns.
 #include <cuda.h>
@@ -57,6 +58,8 @@ constexpr int kEpiCols = kTileN / 2;
 constexpr int kSmallK = 2048;  // reduction elements between drains of the small accumulator
 constexpr int kWriteK = 1024;  // reduction elements between ChiJob write-outs
 constexpr int kTmemCols = 512;
+constexpr int kMainBufs = 3;   // main accumulators: TMEM columns [0, 384)
+constexpr uint32_t kSmallCol = 384;  // the small accumulator: columns [384, 512)
 constexpr uint32_t kSuspendNs = 20000;            // longest suspension of one try_wait
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -517,11 +520,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOperandBytes + L::kStagingBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
-  uint64_t* main_full = bars + 2 * kStages;  // [2] main accumulator buffers
-  uint64_t* main_empty = main_full + 2;
-  uint64_t* small_full = main_empty + 2;     // [2] small accumulator buffers
-  uint64_t* small_empty = small_full + 2;
-  uint64_t* drain = small_empty + 2;
+  uint64_t* main_full = bars + 2 * kStages;  // [kMainBufs] main accumulator buffers
+  uint64_t* main_empty = main_full + kMainBufs;
+  uint64_t* small_full = main_empty + kMainBufs;  // the small accumulator
+  uint64_t* small_empty = small_full + 1;
+  uint64_t* drain = small_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -531,12 +534,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kMainBufs; ++b) {
       mbar_init(&main_full[b], 1);
       mbar_init(&main_empty[b], kEpiWarps);
-      mbar_init(&small_full[b], 1);
-      mbar_init(&small_empty[b], kEpiWarps);
     }
+    mbar_init(small_full, 1);
+    mbar_init(small_empty, kEpiWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -621,18 +624,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = desc_sw128(st), db = desc_sw128(st + S * L::kTileBytes);
 #pragma unroll
           for (int k = 0; k < kSub; ++k) {
-            const int mb = chunk & 1, sb = schunk & 1;
+            const int mb = chunk % kMainBufs;
             if (ok && sub == 0) {
-              ok = mbar_wait(&main_empty[mb], ((static_cast<uint32_t>(chunk) >> 1) & 1u) ^ 1u,
+              ok = mbar_wait(&main_empty[mb], ((static_cast<uint32_t>(chunk / kMainBufs)) & 1u) ^ 1u,
                              abort_flag);
               if (ok && cin == 0)
-                ok = mbar_wait(&small_empty[sb], ((static_cast<uint32_t>(schunk) >> 1) & 1u) ^ 1u,
-                               abort_flag);
+                ok = mbar_wait(small_empty, (static_cast<uint32_t>(schunk) & 1u) ^ 1u, abort_flag);
               tc_fence_after();
             }
             if (ok) {
               const uint32_t d_main = tmem + static_cast<uint32_t>(mb * 128);
-              const uint32_t d_small = tmem + 256u + static_cast<uint32_t>(sb * 128);
+              const uint32_t d_small = tmem + kSmallCol;
               const uint64_t koff = static_cast<uint64_t>((k * kMmaK * 2) >> 4);
               mma_bf16(d_main, da + koff, db + koff, idesc, sub == 0 ? 0u : 1u);
               const bool fresh = (sub == 0 && cin == 0);
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ++chunk;
                 sub = 0;
                 if (++cin == cad.small_every || js == nsub) {
-                  mma_commit(&small_full[sb]);
+                  mma_commit(small_full);
                   ++schunk;
                   cin = 0;
                 }
@@ -699,8 +701,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
       int cin = 0;
       for (long long c = 0; c < nch; ++c, ++chunk) {
-        const int mb = chunk & 1;
-        if (!mbar_wait(&main_full[mb], (static_cast<uint32_t>(chunk) >> 1) & 1u, abort_flag)) {
+        const int mb = chunk % kMainBufs;
+        if (!mbar_wait(&main_full[mb], static_cast<uint32_t>(chunk / kMainBufs) & 1u, abort_flag)) {
           ok = false;
           break;
         }
@@ -710,16 +712,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&main_empty[mb]);
         if (++cin == cad.small_every || c + 1 == nch) {
-          const int sb = schunk & 1;
-          if (!mbar_wait(&small_full[sb], (static_cast<uint32_t>(schunk) >> 1) & 1u, abort_flag)) {
+          if (!mbar_wait(small_full, static_cast<uint32_t>(schunk) & 1u, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          tmem_add64(row_addr + 256u + static_cast<uint32_t>(sb * 128), acc);
+          tmem_add64(row_addr + kSmallCol, acc);
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&small_empty[sb]);
+          if (lane == 0) mbar_arrive(small_empty);
           ++schunk;
           cin = 0;
         }

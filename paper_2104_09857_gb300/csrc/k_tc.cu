@@ -18,10 +18,11 @@
 //             the panel's lambda functions, PT = transposed 3c panel), split
 //             into bf16 slices and scattered into X or Y, with the squared
 //             Frobenius norms of its atom blocks accumulated on the way.
-// Warp roles (320 threads):
+// Warp roles (576 threads):
 //   warp 0      TMA producer (one thread): A and B slices of each K step
 //   warp 1      TMEM allocator and MMA issuer (one thread)
-//   warps 2..9  epilogue: the TMEM accumulators are read into an FP32
+//   warps 2..17 epilogue (4 lane quadrants x 4 groups of 32 columns): the
+//               TMEM accumulators are read into an FP32
 //               register sum per element; the job writes it out at the end
 //               of a tile (ChiJob also every kWriteK reduction elements).
 // The tensor cores' FP32 accumulation rounds each MMA step's result toward
@@ -52,11 +53,11 @@ constexpr int kTileM = 128;
 constexpr int kTileN = 128;
 constexpr int kStageK = 64;   // bf16 elements per K step: one 128-byte swizzled row
 constexpr int kMmaK = 16;
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
-constexpr int kEpiCols = kTileN / 2;
+constexpr int kEpiWarps = 16;                 // 4 TMEM lane quadrants x 4 column groups
+constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr int kEpiCols = kTileN / 4;          // accumulator columns per epilogue warp
 constexpr int kSmallK = 2048;  // reduction elements between drains of the small accumulator
-constexpr int kWriteK = 1024;  // reduction elements between ChiJob write-outs
+constexpr int kWriteK = 2048;  // reduction elements between ChiJob write-outs (one per split-K unit)
 constexpr int kTmemCols = 512;
 constexpr int kMainBufs = 3;   // main accumulators: TMEM columns [0, 384)
 constexpr uint32_t kSmallCol = 384;  // the small accumulator: columns [384, 512)
@@ -179,24 +180,39 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-// acc[j] += TMEM[lane row][taddr column + j], j < 64: two 32-column loads,
-// each followed by its wait (the registers pass through the wait's asm so
-// that no use of them can be scheduled before it).  The 320-thread block
-// leaves 168 registers per thread, too few for one 64-column load.
-__device__ __forceinline__ void tmem_add64(uint32_t taddr, float (&acc)[64]) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
+// acc[j] += TMEM[lane row][taddr column + j], j < 32: one 32-column load and
+// its wait, or (kHalves = 2) two 16-column loads and waits, which keeps 16
+// fewer registers live.  The registers pass through the wait's asm so that
+// no use of them can be scheduled before it.
+template <int kHalves>
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
+  if (kHalves == 1) {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr + static_cast<uint32_t>(h * 32)));
+        : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
                  :
                  : "memory");
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[h * 32 + j] += __uint_as_float(r[j]);
+    for (int k = 0; k < 32; ++k) acc[k] += __uint_as_float(r[k]);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr + static_cast<uint32_t>(h * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;"
+                   : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                   :
+                   : "memory");
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[h * 16 + k] += __uint_as_float(r[k]);
+    }
   }
 }
 // Drain cadence of the persistent kernel, in MMA steps of kMmaK reduction
@@ -207,9 +223,11 @@ struct Cadence {
   int main, small_every, write_every;
 };
 
-// Per-epilogue-warp staging for coalesced stores: 32 rows x 34 bf16, or
-// 32 rows x 17 floats (both 2176 bytes).
-constexpr int kStgBytes = 2176;
+// Per-epilogue-warp staging: 32 rows x kStgCols floats, row pitch
+// kStgCols + 1 (no bank conflicts on column reads).
+constexpr int kStgCols = 8;
+constexpr int kStgPitch = kStgCols + 1;
+constexpr int kStgBytes = 32 * kStgPitch * 4;
 
 template <int S>
 struct Smem {
@@ -238,6 +256,7 @@ struct ChiJob {
   double* chi;
   float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
   static constexpr bool kPeriodic = true;
+  static constexpr int kDrainHalves = 2;  // 96 registers: one 32-column load would spill
 
   struct Tile {
     int ya, yb, cnt;
@@ -290,42 +309,44 @@ struct ChiJob {
       return x;
     }
   };
-  // Add the register sums of a warp (rows quad*32.., 64 columns from c0) into
-  // chi, 16 columns at a time through the warp's staging buffer so that each
-  // store instruction covers two rows of 16 consecutive doubles.
+  // Add the register sums of a warp (rows quad*32.., kEpiCols columns from
+  // c0) into chi, kStgCols columns at a time through the warp's staging
+  // buffer, so that each store instruction covers 4 rows of 8 consecutive
+  // doubles.
   __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
                         uint8_t* stg) const {
-    float* f = reinterpret_cast<float*>(stg);  // [32][17]
+    float* f = reinterpret_cast<float*>(stg);  // [32][kStgPitch]
+    constexpr int kRowsPer = 32 / kStgCols;    // rows covered by one warp store
 #pragma unroll
-    for (int cc = 0; cc < kEpiCols; cc += 16) {
+    for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) f[lane * 17 + j] = acc[cc + j];
+      for (int j = 0; j < kStgCols; ++j) f[lane * kStgPitch + j] = acc[cc + j];
       __syncwarp();
-      const int col = lane & 15, sub = lane >> 4;
+      const int col = lane % kStgCols, sub = lane / kStgCols;
       const int q = T.yb + c0 + cc + col;
       if (unit_first) {
         // units of one tile may run concurrently when K is split
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
+        for (int i = 0; i < 32; i += kRowsPer) {
           const int p = T.ya + quad * 32 + i + sub;
           if (p < prow && q < nri)
             atomicAdd(chi + static_cast<long long>(P0 + p) * nri + q,
-                      -static_cast<double>(f[(i + sub) * 17 + col] * out_scale));
+                      -static_cast<double>(f[(i + sub) * kStgPitch + col] * out_scale));
         }
       } else {
-        // one owner per tile: all 16 loads in flight, then the stores
-        double old[16];
+        // one owner per tile: all loads in flight, then the stores
+        double old[32 / kRowsPer];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int p = T.ya + quad * 32 + 2 * i + sub;
+        for (int i = 0; i < 32 / kRowsPer; ++i) {
+          const int p = T.ya + quad * 32 + kRowsPer * i + sub;
           old[i] = (p < prow && q < nri) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int p = T.ya + quad * 32 + 2 * i + sub;
+        for (int i = 0; i < 32 / kRowsPer; ++i) {
+          const int p = T.ya + quad * 32 + kRowsPer * i + sub;
           if (p < prow && q < nri)
             chi[static_cast<long long>(P0 + p) * nri + q] =
-                old[i] - static_cast<double>(f[(2 * i + sub) * 17 + col] * out_scale);
+                old[i] - static_cast<double>(f[(kRowsPer * i + sub) * kStgPitch + col] * out_scale);
         }
       }
       __syncwarp();
@@ -378,6 +399,7 @@ struct PanelJob {
   float unscale;              // 1 / (scale of Gg x scale of PT): true Z = acc * unscale
   float out_scale;            // scale of the Z slices
   static constexpr bool kPeriodic = false;
+  static constexpr int kDrainHalves = 1;
 
   struct Tile {
     int ya, yb, ksteps, task, mt, nt;
@@ -409,13 +431,13 @@ struct PanelJob {
       return v;
     }
   };
-  // The 64 register sums go through the thread's own staging row 16 at a
+  // The register sums go through the thread's own staging row kStgCols at a
   // time, so that the per-column loops stay rolled (small code).
   __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
                         uint8_t* stg) const {
     const PanelTaskTC& tk = tasks[T.task];
     const bool f = f16 != 0;
-    float* fr = reinterpret_cast<float*>(stg) + lane * 17;
+    float* fr = reinterpret_cast<float*>(stg) + lane * kStgPitch;
     if (mode == 0) {
       // row n = (pw, s') of the owner's panel; columns mu = G rows
       const int n = T.mt * kTileM + quad * 32 + lane;
@@ -430,11 +452,11 @@ struct PanelJob {
       int mend = ao_off[m + 1];
       float ss = 0.f;
 #pragma unroll
-      for (int cc = 0; cc < kEpiCols; cc += 16) {
+      for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) fr[j] = acc[cc + j];
+        for (int j = 0; j < kStgCols; ++j) fr[j] = acc[cc + j];
 #pragma unroll 1
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < kStgCols; ++j) {
           const int mu = mu0 + cc + j;
           if (mu >= rows_valid) break;  // warp-uniform
           float v = fr[j] * unscale;
@@ -466,11 +488,11 @@ struct PanelJob {
       const int row_key = r_ok ? (s_local * n_at + tk.owner) * n_at : -1;
       float ss = 0.f;
 #pragma unroll
-      for (int cc = 0; cc < kEpiCols; cc += 16) {
+      for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) fr[j] = acc[cc + j];
+        for (int j = 0; j < kStgCols; ++j) fr[j] = acc[cc + j];
 #pragma unroll 1
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < kStgCols; ++j) {
           const int n = n0 + cc + j;
           if (n >= tk.N) break;  // warp-uniform
           float v = fr[j] * unscale;
@@ -684,10 +706,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    // ---------------- epilogue (warps 2..17) ----------------
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const int c0 = half * kEpiCols;
+    const int cgroup = (warp - 2) >> 2;  // warps 2..17: 4 per column group, one per lane quadrant
+    const int c0 = cgroup * kEpiCols;
     uint8_t* stg = staging + (warp - 2) * kStgBytes;
     const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0);
     float acc[kEpiCols];
@@ -707,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        tmem_add64(row_addr + static_cast<uint32_t>(mb * 128), acc);
+        tmem_add32<Job::kDrainHalves>(row_addr + static_cast<uint32_t>(mb * 128), acc);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&main_empty[mb]);
@@ -717,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          tmem_add64(row_addr + kSmallCol, acc);
+          tmem_add32<Job::kDrainHalves>(row_addr + kSmallCol, acc);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(small_empty);

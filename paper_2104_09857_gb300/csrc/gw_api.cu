@@ -145,6 +145,7 @@ void reset_tensor(gw_ctx* ctx) {
   free_dev(ctx->d_pt);
   ctx->d_pt = nullptr;
   ctx->pt_ok = false;
+  ctx->ycov_valid = false;
 }
 
 void reset_greens(gw_ctx* ctx) {
@@ -164,6 +165,7 @@ struct Timer {
 // ---------------------------------------------------------------------------
 int build_panels(gw_ctx* ctx, double thr) {
   if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
+  ctx->ycov_valid = false;
   const int n = ctx->n_at;
   std::vector<int> kept;
   kept.reserve(ctx->n_blocks);
@@ -638,6 +640,43 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
   return GW_OK;
 }
 
+// Owners covering each RI row (for zeroing only the unwritten part of Y):
+// once per panel build.
+int ensure_ycover(gw_ctx* ctx) {
+  if (ctx->ycov_valid) return GW_OK;
+  free_dev(ctx->d_ycov_lo);
+  free_dev(ctx->d_ycov_hi);
+  ctx->d_ycov_lo = ctx->d_ycov_hi = nullptr;
+  const int nri = ctx->nri;
+  std::vector<int> lo(nri, INT32_MAX), hi(nri, -1), cnt(nri, 0);
+  for (int m = 0; m < ctx->n_at; ++m) {
+    const PanelDesc& d = ctx->panels[m];
+    if (d.K == 0) continue;
+    for (int q = d.p0; q < d.p0 + d.npw; ++q) {
+      lo[q] = std::min(lo[q], m);
+      hi[q] = std::max(hi[q], m);
+      ++cnt[q];
+    }
+  }
+  bool ok = true;
+  for (int q = 0; q < nri && ok; ++q) {
+    if (cnt[q] == 0) {
+      lo[q] = -1;
+      hi[q] = -1;
+    } else if (hi[q] - lo[q] + 1 != cnt[q]) {
+      ok = false;
+    }
+  }
+  ctx->ycov_valid = true;
+  ctx->ycov_ok = ok;
+  if (!ok) return GW_OK;
+  GW_TRY(cudaMalloc(&ctx->d_ycov_lo, std::max(nri, 1) * sizeof(int)));
+  GW_TRY(cudaMalloc(&ctx->d_ycov_hi, std::max(nri, 1) * sizeof(int)));
+  GW_TRY(cudaMemcpy(ctx->d_ycov_lo, lo.data(), nri * sizeof(int), cudaMemcpyHostToDevice));
+  GW_TRY(cudaMemcpy(ctx->d_ycov_hi, hi.data(), nri * sizeof(int), cudaMemcpyHostToDevice));
+  return GW_OK;
+}
+
 // One batch on the tensor cores: steps A and B straight into bf16 slices,
 // block filter from the accumulated norms, task lists, step C.
 int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const double* g_virt,
@@ -662,7 +701,19 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = ws(ctx, "Xs", (size_t)slices * prow * Kb * 2, &xs))) return rc;
   if ((rc = ws(ctx, "Ys", (size_t)slices * nri * Kb * 2, &ys))) return rc;
   GW_TRY(cudaMemsetAsync(xs, 0, (size_t)slices * prow * Kb * 2, ctx->stream));
-  GW_TRY(cudaMemsetAsync(ys, 0, (size_t)slices * nri * Kb * 2, ctx->stream));
+  if ((rc = ensure_ycover(ctx))) return rc;
+  if (ctx->ycov_ok) {
+    // step B writes every (q, s, mu of a covering owner, sigma); zero the rest
+    long long* d_seg0;
+    int* d_nao0;
+    if ((rc = upload(ctx, "seg_y", b.seg, &d_seg0))) return rc;
+    if ((rc = upload(ctx, "n_ao_y", ctx->n_ao, &d_nao0))) return rc;
+    gw::launch_zero_unwritten_y(ys, slices, (long long)nri * Kb, Kb, nri, ns, d_seg0, d_nao0, b.s0,
+                                ctx->d_ao_off, ctx->naop, ctx->d_ycov_lo, ctx->d_ycov_hi, ctx->stream);
+    GW_CHECK_LAUNCH();
+  } else {
+    GW_TRY(cudaMemsetAsync(ys, 0, (size_t)slices * nri * Kb * 2, ctx->stream));
+  }
   const int pa0 = [&] {
     int a = 0;
     while (ctx->ri_off[a + 1] <= b.P0) ++a;
@@ -676,15 +727,14 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = wsT(ctx, "by2", (size_t)ns * n_at * n_at, &by2))) return rc;
   GW_TRY(cudaMemsetAsync(bx2, 0, (size_t)ns * n_at * npa * sizeof(float), ctx->stream));
   GW_TRY(cudaMemsetAsync(by2, 0, (size_t)ns * n_at * n_at * sizeof(float), ctx->stream));
-  int* d_err;
+  int* d_err;  // zeroed once per tau point by gw_chi_tau
   if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
-  GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
   CUtensorMap mp;
   if (gw::make_slice_map(&mp, ctx->d_pt, kmax, ctx->pt_rows, slices, tile, f16))
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
   double issued = 0.0;
   cudaEvent_t ea0, ea1;
-  if ((rc = c_event_pair(ctx, 1000 + batch_idx, &ea0, &ea1))) return rc;
+  if ((rc = c_event_pair(ctx, (size_t{1} << 20) + batch_idx, &ea0, &ea1))) return rc;
   GW_TRY(cudaEventRecord(ea0, ctx->stream));
 
   // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu ----
@@ -801,12 +851,16 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   int* d_nao;
   if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
   if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao))) return rc;
+  // queue of filtered blocks to zero (shared by the two stream-ordered calls)
+  int *zlist, *zcount;
+  if ((rc = wsT(ctx, "zlist", (size_t)ns * n_at * n_at, &zlist))) return rc;
+  if ((rc = wsT(ctx, "zcount", 1, &zcount))) return rc;
   gw::launch_slices_block_filter(xs, slices, (long long)prow * Kb, Kb, b.P0, ctx->d_ri_off,
-                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, pa0, npa, n_at, thr,
-                                 ctx->naop, bx2, bx, fx, npt, tile, ctx->stream);
+                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, pa0, npa, n_at, thr, bx2, bx,
+                                 fx, npt, tile, zlist, zcount, ctx->stream);
   gw::launch_slices_block_filter(ys, slices, (long long)nri * Kb, Kb, 0, ctx->d_ri_off, ctx->d_ao_off,
-                                 d_nao, b.s0, ns, d_seg, 0, n_at, n_at, thr, ctx->naop, by2, by, fy,
-                                 nqt, tile, ctx->stream);
+                                 d_nao, b.s0, ns, d_seg, 0, n_at, n_at, thr, by2, by, fy, nqt, tile,
+                                 zlist, zcount, ctx->stream);
   GW_CHECK_LAUNCH();
   std::vector<long long> slab_k0(nslab);
   std::vector<int> slab_len(nslab);
@@ -911,47 +965,45 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     // elements
     std::vector<int> h_tasks((size_t)npt * nqt * nslab);
     GW_TRY(cudaMemcpy(h_tasks.data(), tasks, h_tasks.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    // active tiles in grouped raster order (groups of 8 row tiles swept
+    // along the columns)
     std::vector<int> raster;
-    for (size_t t = 0; t < h_counts.size(); ++t)
-      if (h_counts[t] > 0) raster.push_back((int)t);
-    std::stable_sort(raster.begin(), raster.end(), [&](int a, int c) {
-      const int pa = a / nqt, qa = a % nqt, pc = c / nqt, qc = c % nqt;
-      if (pa / 8 != pc / 8) return pa / 8 < pc / 8;
-      if (qa != qc) return qa < qc;
-      return pa < pc;
-    });
-    std::vector<std::vector<std::pair<int, int>>> segs(raster.size());
-    for (size_t r = 0; r < raster.size(); ++r) {
-      const int t = raster[r];
+    for (int pg = 0; pg < npt; pg += 8)
+      for (int qt = 0; qt < nqt; ++qt)
+        for (int pt = pg; pt < std::min(npt, pg + 8); ++pt)
+          if (h_counts[(size_t)pt * nqt + qt] > 0) raster.push_back(pt * nqt + qt);
+    // units: runs of a tile's slab list of about c_split_k elements, keyed by
+    // their first slab (slab ids follow the reduction index)
+    std::vector<int> r_tile, r_first, r_count, r_key;
+    for (const int t : raster) {
       const int* lst = &h_tasks[(size_t)t * nslab];
       int i0 = 0;
       long long kk = 0;
       for (int i = 0; i < h_counts[t]; ++i) {
         kk += slab_len[lst[i]];
         if (kk >= ctx->c_split_k || i == h_counts[t] - 1) {
-          segs[r].push_back({i0, i + 1 - i0});
+          r_tile.push_back(t);
+          r_first.push_back(i0);
+          r_count.push_back(i + 1 - i0);
+          r_key.push_back(lst[i0]);
           i0 = i + 1;
           kk = 0;
         }
       }
     }
-    // units in order of their first reduction index (then raster): CTAs that
-    // run side by side stream the same K window of X and Y through L2
-    struct Unit {
-      long long k0;
-      int tile, first, count;
-    };
-    std::vector<Unit> units;
-    for (size_t r = 0; r < raster.size(); ++r)
-      for (const auto& sg : segs[r])
-        units.push_back({slab_k0[h_tasks[(size_t)raster[r] * nslab + sg.first]], raster[r], sg.first,
-                         sg.second});
-    std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& c) { return a.k0 < c.k0; });
-    std::vector<int> u_tile, u_first, u_count;
-    for (const Unit& u : units) {
-      u_tile.push_back(u.tile);
-      u_first.push_back(u.first);
-      u_count.push_back(u.count);
+    // order by first reduction index, raster order among equal keys
+    // (counting sort): CTAs that run side by side stream the same K window
+    // of X and Y through L2
+    std::vector<int> start((size_t)nslab + 1, 0);
+    for (const int k : r_key) ++start[(size_t)k + 1];
+    for (int k = 0; k < nslab; ++k) start[(size_t)k + 1] += start[k];
+    const size_t nu = r_key.size();
+    std::vector<int> u_tile(nu), u_first(nu), u_count(nu);
+    for (size_t u = 0; u < nu; ++u) {
+      const int pos = start[r_key[u]]++;
+      u_tile[pos] = r_tile[u];
+      u_first[pos] = r_first[u];
+      u_count[pos] = r_count[u];
     }
     int *d_ut, *d_uf, *d_uc;
     if ((rc = upload(ctx, "unit_tile", u_tile, &d_ut))) return rc;
@@ -976,20 +1028,14 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   GW_TRY(cudaEventRecord(ec1, ctx->stream));
   ctx->stats.c_launches += 1;
   ctx->stats.kernel_launches += 1;
-  std::vector<double> h_fc((size_t)ns * n_at);
-  int h_err = 0;
-  GW_TRY(cudaMemcpyAsync(h_fc.data(), d_fc, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                         ctx->stream));
-  GW_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  GW_TRY(cudaStreamSynchronize(ctx->stream));
-  if (h_err)
-    return fail(ctx, GW_ERR_TIMEOUT,
-                "tensor-core kernel: a bounded wait gave up (flags " + std::to_string(h_err) + ")");
-  float ms_ck = 0.f, ms_ab = 0.f;
-  GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
-  GW_TRY(cudaEventElapsedTime(&ms_ab, ea0, ea1));
-  ctx->stats.ms_step_c_kernel += ms_ck;
-  ctx->stats.ms_step_ab += ms_ab;
+  // this batch's flop counts, error flag and timings are read at the end of
+  // the tau point (tc_finish_tau), so the next batch is queued without a wait
+  double* d_fc_all;  // sized n_at * n_at by gw_chi_tau
+  if ((rc = wsT(ctx, "fc_all", (size_t)n_at * n_at, &d_fc_all))) return rc;
+  GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * n_at * sizeof(double),
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * n_at, fc_scale});
+  ctx->tc_fc_used += (long long)ns * n_at;
   long long act = 0, sl_act = 0;
   double ksum = 0.0;
   for (size_t t = 0; t < h_counts.size(); ++t) {
@@ -1001,8 +1047,54 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   ctx->stats.tiles_active += act;
   ctx->stats.slabs_total += (long long)npt * nqt * nslab;
   ctx->stats.slabs_active += sl_act;
-  for (double v : h_fc) fc_host.push_back(v * fc_scale);
+  (void)fc_host;
   ctx->stats.flops_issued += issued + 2.0 * tile * tile * ksum * prods;
+  return GW_OK;
+}
+
+// Start of a tau point on the tensor-core route: error flag and flop-count
+// staging for its batches.
+int tc_begin_tau(gw_ctx* ctx) {
+  int* d_err;
+  double* d_fc_all;
+  int rc;
+  if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
+  if ((rc = wsT(ctx, "fc_all", (size_t)ctx->n_at * ctx->n_at, &d_fc_all))) return rc;
+  GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+  ctx->tc_pending.clear();
+  ctx->tc_fc_used = 0;
+  return GW_OK;
+}
+
+// End of a tau point (after the stream is synchronised): error flag, step
+// timings and step-C flop counts of its tensor-core batches.
+int tc_finish_tau(gw_ctx* ctx, std::vector<double>& fc_host) {
+  int* d_err;
+  double* d_fc_all;
+  int rc;
+  if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
+  if ((rc = wsT(ctx, "fc_all", (size_t)ctx->n_at * ctx->n_at, &d_fc_all))) return rc;
+  int h_err = 0;
+  GW_TRY(cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_err)
+    return fail(ctx, GW_ERR_TIMEOUT,
+                "tensor-core kernel: a bounded wait gave up (flags " + std::to_string(h_err) + ")");
+  std::vector<double> h_fc((size_t)ctx->tc_fc_used);
+  if (!h_fc.empty())
+    GW_TRY(cudaMemcpy(h_fc.data(), d_fc_all, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (const auto& p : ctx->tc_pending) {
+    cudaEvent_t ec0, ec1, ea0, ea1;
+    if ((rc = c_event_pair(ctx, p.batch_idx, &ec0, &ec1))) return rc;
+    if ((rc = c_event_pair(ctx, (size_t{1} << 20) + p.batch_idx, &ea0, &ea1))) return rc;
+    float ms_ck = 0.f, ms_ab = 0.f;
+    GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
+    GW_TRY(cudaEventElapsedTime(&ms_ab, ea0, ea1));
+    ctx->stats.ms_step_c_kernel += ms_ck;
+    ctx->stats.ms_step_ab += ms_ab;
+    for (int i = 0; i < p.fc_n; ++i) fc_host.push_back(h_fc[(size_t)p.fc_off + i] * p.fc_scale);
+  }
+  ctx->tc_pending.clear();
+  ctx->tc_fc_used = 0;
   return GW_OK;
 }
 
@@ -1058,6 +1150,8 @@ void gw_destroy(gw_ctx* ctx) {
   free_dev(ctx->d_mlp_wb);
   free_dev(ctx->d_mlp_m);
   free_dev(ctx->d_mlp_v);
+  free_dev(ctx->d_ycov_lo);
+  free_dev(ctx->d_ycov_hi);
   for (cudaEvent_t e : c_events(ctx)) cudaEventDestroy(e);
   c_events(ctx).clear();
   auto& reg = work_registry();
@@ -1409,6 +1503,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     GW_TRY(cudaMemsetAsync(acc, 0, (size_t)nri * nri * sizeof(double), ctx->stream));
     GW_TRY(cudaEventRecord(ev[1], ctx->stream));
     std::vector<double> fc;
+    if (tcpath && (rc = tc_begin_tau(ctx))) return rc;
     for (size_t bi = 0; bi < batches.size(); ++bi) {
       const Batch& b = batches[bi];
       if (f64)
@@ -1428,6 +1523,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
       GW_TRY(cudaMemcpyAsync(chi_out + (size_t)(j - tau_first) * nri * nri, stage,
                              (size_t)nri * nri * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     GW_TRY(cudaStreamSynchronize(ctx->stream));
+    if (tcpath && (rc = tc_finish_tau(ctx, fc))) return rc;
     float t01, t12;
     GW_TRY(cudaEventElapsedTime(&t01, ev[0], ev[1]));
     GW_TRY(cudaEventElapsedTime(&t12, ev[1], ev[2]));

@@ -143,6 +143,22 @@ struct gw_ctx {
   long long pt_rows = 0;
   int pt_kmax = 0;
   std::vector<gw::PanelTaskTC> pt_tasks;  // per atom (K == 0: none)
+  // per RI row q: the owner atoms whose panel windows cover q, [ycov_lo,
+  // ycov_hi] (lo < 0: none); valid when they are contiguous for every q
+  // tensor-core batches of the current tau point whose flop counts and
+  // timings are read once at its end (no per-batch host synchronisation)
+  struct TcPending {
+    size_t batch_idx;
+    long long fc_off;
+    int fc_n;
+    double fc_scale;
+  };
+  std::vector<TcPending> tc_pending;
+  long long tc_fc_used = 0;
+  bool ycov_valid = false;  // cleared whenever the panels are rebuilt
+  bool ycov_ok = false;
+  int* d_ycov_lo = nullptr;
+  int* d_ycov_hi = nullptr;
 
   // learned screening: network (FP32 master, bf16 copy, Adam moments)
   float* d_mlp_theta = nullptr;

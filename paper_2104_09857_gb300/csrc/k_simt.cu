@@ -202,10 +202,14 @@ __device__ __forceinline__ void tile_nt_run(const T* __restrict__ A, long long l
     for (int j = 0; j < 4; ++j) acc64[i][j] += (double)acc[i][j];
 }
 
-// G = Cs Cs^T (full K), written (not accumulated) into g[m][n].
+// G = Cs Cs^T (full K), written (not accumulated) into g[m][n]: tiles on
+// and above the diagonal are computed and also stored transposed, so G is
+// exactly symmetric (inside a diagonal tile both halves use the same k order
+// and commutative products).
 __global__ void k_syrk64(const double* __restrict__ cs, int nao, int K, double* __restrict__ g) {
   __shared__ double As[16][65];
   __shared__ double Bs[16][65];
+  if (blockIdx.x < blockIdx.y) return;
   int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   double acc[4][4] = {};
   if (K > 0)
@@ -217,7 +221,10 @@ __global__ void k_syrk64(const double* __restrict__ cs, int nao, int K, double* 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-      if (m < nao && n < nao) g[(long long)m * nao + n] = acc[i][j];
+      if (m < nao && n < nao) {
+        g[(long long)m * nao + n] = acc[i][j];
+        if (m0 != n0) g[(long long)n * nao + m] = acc[i][j];
+      }
     }
 }
 

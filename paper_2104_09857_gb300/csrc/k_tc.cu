@@ -817,46 +817,96 @@ __global__ void k_transpose_panel(const double* __restrict__ pool, const PanelTa
   }
 }
 
-// Norms of the atom blocks of an operand from the accumulated squares; zero
-// the filtered ones (norm < thr, norm > 0) in every slice; flag the kept
-// nonzero blocks and the (slab, tile) pairs they touch.
-__global__ void k_slices_block_filter(uint16_t* __restrict__ Z, int slices, long long slice_elems,
-                                      long long ldk, int rowoff, const int* __restrict__ ri_off,
-                                      const int* __restrict__ ao_off, const int* __restrict__ n_ao,
-                                      int s0, int ns, const long long* __restrict__ seg, int pa0,
-                                      int npa, int n_at, double thr, int naop,
-                                      const float* __restrict__ norm2,
-                                      unsigned char* __restrict__ blockflag,
-                                      unsigned char* __restrict__ tileflag, int ntile,
-                                      int tile_rows) {
-  long long w = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+// Norms of the atom blocks of an operand from the accumulated squares, one
+// thread per block (sigma-atom, mu-atom, RI atom): flag the kept nonzero
+// blocks and the (slab, tile) pairs they touch; queue the filtered nonzero
+// ones (norm < thr) for zeroing.
+__global__ void k_slices_block_flags(const int* __restrict__ ri_off, int rowoff, int pa0, int npa,
+                                     int n_at, int ns, double thr, const float* __restrict__ norm2,
+                                     unsigned char* __restrict__ blockflag,
+                                     unsigned char* __restrict__ tileflag, int ntile, int tile_rows,
+                                     int* __restrict__ zlist, int* __restrict__ zcount) {
   const long long nblk = static_cast<long long>(ns) * n_at * npa;
-  if (w >= nblk) return;
-  const int pl = static_cast<int>(w % npa);
-  const long long t = w / npa;
-  const int m = static_cast<int>(t % n_at);
-  const int sl = static_cast<int>(t / n_at);
-  const int s = s0 + sl, p = pa0 + pl;
-  const double nrm = sqrt(static_cast<double>(norm2[w]));
-  const bool kept = !(nrm < thr);
-  const bool nz = kept && nrm > 0.0;
-  if (lane == 0) blockflag[w] = nz;
-  const int nsig = n_ao[s];
-  const int rows0 = ri_off[p] - rowoff, nrows = ri_off[p + 1] - ri_off[p];
-  const long long c0 = seg[sl] + static_cast<long long>(ao_off[m]) * nsig;
-  const int ncols = n_ao[m] * nsig;
-  if (!kept && nrm > 0.0) {
+  for (long long w = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; w < nblk;
+       w += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int pl = static_cast<int>(w % npa);
+    const long long t = w / npa;  // sl * n_at + m
+    const double nrm = sqrt(static_cast<double>(norm2[w]));
+    const bool kept = !(nrm < thr);
+    const bool nz = kept && nrm > 0.0;
+    blockflag[w] = nz;
+    if (!kept && nrm > 0.0) zlist[atomicAdd(zcount, 1)] = static_cast<int>(w);
+    if (nz) {
+      const int p = pa0 + pl;
+      const int rows0 = ri_off[p] - rowoff, nrows = ri_off[p + 1] - ri_off[p];
+      const int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
+      for (int tt = ts; tt <= te; ++tt) tileflag[t * ntile + tt] = 1;
+    }
+  }
+}
+
+// Zero, in every slice, the blocks queued by k_slices_block_flags: one warp
+// per queued block, the warps striding over the queue.
+__global__ void k_slices_zero_blocks(uint16_t* __restrict__ Z, int slices, long long slice_elems,
+                                     long long ldk, int rowoff, const int* __restrict__ ri_off,
+                                     const int* __restrict__ ao_off, const int* __restrict__ n_ao,
+                                     int s0, const long long* __restrict__ seg, int pa0, int npa,
+                                     int n_at, const int* __restrict__ zlist,
+                                     const int* __restrict__ zcount) {
+  const int lane = threadIdx.x & 31;
+  const int nq = *zcount;
+  const int nwarps = gridDim.x * (blockDim.x / 32);
+  for (int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < nq; q += nwarps) {
+    const long long w = zlist[q];
+    const int pl = static_cast<int>(w % npa);
+    const long long t = w / npa;
+    const int m = static_cast<int>(t % n_at);
+    const int sl = static_cast<int>(t / n_at);
+    const int nsig = n_ao[s0 + sl];
+    const int p = pa0 + pl;
+    const int rows0 = ri_off[p] - rowoff, nrows = ri_off[p + 1] - ri_off[p];
+    const long long c0 = seg[sl] + static_cast<long long>(ao_off[m]) * nsig;
+    const int ncols = n_ao[m] * nsig;
     for (int r = 0; r < nrows; ++r)
       for (int c = lane; c < ncols; c += 32)
         for (int sc = 0; sc < slices; ++sc)
           Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = 0;  // +0 in both formats
   }
-  if (nz) {
-    const int ts = rows0 / tile_rows, te = (rows0 + nrows - 1) / tile_rows;
-    for (int tt = ts + lane; tt <= te; tt += 32)
-      tileflag[(static_cast<long long>(sl) * n_at + m) * ntile + tt] = 1;
-    (void)naop;
+}
+
+// Zero n 16-bit elements from p with the whole CTA (16-byte stores in the
+// aligned body).
+__device__ __forceinline__ void zero_run(uint16_t* p, long long n) {
+  long long head = (8 - static_cast<long long>((reinterpret_cast<uintptr_t>(p) >> 1) & 7)) & 7;
+  if (head > n) head = n;
+  for (long long i = threadIdx.x; i < head; i += blockDim.x) p[i] = 0;
+  uint4* q = reinterpret_cast<uint4*>(p + head);
+  const long long nv = (n - head) >> 3;
+  for (long long i = threadIdx.x; i < nv; i += blockDim.x) q[i] = make_uint4(0, 0, 0, 0);
+  for (long long i = head + nv * 8 + threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+// The part of Y that step B does not write: for row Q and batch atom s, the
+// mu outside the atoms [lo[Q], hi[Q]] whose panel windows cover Q (all of
+// the segment when lo[Q] < 0), which includes the padding mu >= n_AO.  One
+// CTA per (Q, s) pair, striding.
+__global__ void k_zero_unwritten_y(uint16_t* __restrict__ Y, int slices, long long slice_elems,
+                                   long long ldk, int nri, int ns, const long long* __restrict__ seg,
+                                   const int* __restrict__ n_ao, int s0,
+                                   const int* __restrict__ ao_off, int naop,
+                                   const int* __restrict__ lo, const int* __restrict__ hi) {
+  const long long npair = static_cast<long long>(nri) * ns;
+  for (long long w = blockIdx.x; w < npair; w += gridDim.x) {
+    const int q = static_cast<int>(w / ns), sl = static_cast<int>(w % ns);
+    const int nsig = n_ao[s0 + sl];
+    const long long L = static_cast<long long>(naop) * nsig;
+    const long long a = lo[q] < 0 ? L : static_cast<long long>(ao_off[lo[q]]) * nsig;
+    const long long b = lo[q] < 0 ? L : static_cast<long long>(ao_off[hi[q] + 1]) * nsig;
+    for (int sc = 0; sc < slices; ++sc) {
+      uint16_t* base = Y + sc * slice_elems + static_cast<long long>(q) * ldk + seg[sl];
+      zero_run(base, a);
+      zero_run(base + b, L - b);
+    }
   }
 }
 
@@ -913,6 +963,14 @@ double pow2_scale(double bound) {
   if (!(bound > 0.0) || !std::isfinite(bound)) return 1.0;
   // the scaled bound is at most 2^14: four times below the binary16 maximum
   return std::ldexp(1.0, 14 - static_cast<int>(std::ceil(std::log2(bound))));
+}
+
+void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int nri, int ns,
+                             const long long* seg, const int* n_ao, int s0, const int* ao_off,
+                             int naop, const int* lo, const int* hi, cudaStream_t st) {
+  if (nri == 0 || ns == 0) return;
+  tc::k_zero_unwritten_y<<<152 * 16, 256, 0, st>>>(static_cast<uint16_t*>(Y), slices, slice_elems, ldk,
+                                                   nri, ns, seg, n_ao, s0, ao_off, naop, lo, hi);
 }
 
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
@@ -1073,13 +1131,20 @@ void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int n
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
                                 const int* ri_off, const int* ao_off, const int* n_ao, int s0,
                                 int ns, const long long* seg, int pa0, int npa, int n_at,
-                                double thr, int naop, const float* norm2, unsigned char* blockflag,
-                                unsigned char* tileflag, int ntile, int tile_rows, cudaStream_t st) {
+                                double thr, const float* norm2, unsigned char* blockflag,
+                                unsigned char* tileflag, int ntile, int tile_rows, int* zlist,
+                                int* zcount, cudaStream_t st) {
   const long long nblk = static_cast<long long>(ns) * n_at * npa;
   if (nblk == 0) return;
-  tc::k_slices_block_filter<<<static_cast<unsigned>((nblk + 7) / 8), 256, 0, st>>>(
-      static_cast<uint16_t*>(Z), slices, slice_elems, ldk, rowoff, ri_off, ao_off, n_ao, s0, ns,
-      seg, pa0, npa, n_at, thr, naop, norm2, blockflag, tileflag, ntile, tile_rows);
+  cudaMemsetAsync(zcount, 0, sizeof(int), st);
+  long long blocks = (nblk + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  tc::k_slices_block_flags<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+      ri_off, rowoff, pa0, npa, n_at, ns, thr, norm2, blockflag, tileflag, ntile, tile_rows, zlist,
+      zcount);
+  tc::k_slices_zero_blocks<<<152 * 4, 256, 0, st>>>(static_cast<uint16_t*>(Z), slices, slice_elems, ldk,
+                                                  rowoff, ri_off, ao_off, n_ao, s0, seg, pa0, npa, n_at,
+                                                  zlist, zcount);
 }
 
 }  // namespace gw

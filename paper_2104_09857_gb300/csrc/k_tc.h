@@ -55,6 +55,13 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
                     const long long* rowbase, const int* rowmul, const int* row_slocal, float* norm2,
                     const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
                     int pa0, int flush_k, int* err_flag, cudaStream_t st);
+// Zero the part of the step-B operand Y that step B does not write: for each
+// RI row q and batch atom s, the mu outside the owner atoms [lo[q], hi[q]]
+// whose panel windows cover q (the whole segment when lo[q] < 0).  Valid
+// when the owners covering each q form one contiguous range.
+void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int nri, int ns,
+                             const long long* seg, const int* n_ao, int s0, const int* ao_off,
+                             int naop, const int* lo, const int* hi, cudaStream_t st);
 // scale * FP64 [rows][cols] (row stride ld) -> `slices` slices [S][rows][kpad],
 // zero-padded in k.
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
@@ -65,10 +72,15 @@ void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int nta
 void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
                              int kmax, int slices, long long slice_elems, int f16, double scale,
                              void* out, cudaStream_t st);
+// Atom-block filter of an operand (X or Y) from the squared norms its panel
+// job accumulated: blockflag = kept and nonzero, tileflag per (sigma-atom,
+// mu-atom, row tile) touched, and the filtered nonzero blocks zeroed in every
+// slice.  zlist (ns * n_at * npa ints) and zcount (one int) are scratch.
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
                                 const int* ri_off, const int* ao_off, const int* n_ao, int s0,
                                 int ns, const long long* seg, int pa0, int npa, int n_at,
-                                double thr, int naop, const float* norm2, unsigned char* blockflag,
-                                unsigned char* tileflag, int ntile, int tile_rows, cudaStream_t st);
+                                double thr, const float* norm2, unsigned char* blockflag,
+                                unsigned char* tileflag, int ntile, int tile_rows, int* zlist,
+                                int* zcount, cudaStream_t st);
 
 }  // namespace gw

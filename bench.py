@@ -274,11 +274,13 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     prec = args.precision
     t_gen = time.perf_counter()
-    case = make_case(WORKLOAD)
+    case = make_case(args.workload)
     t_gen = time.perf_counter() - t_gen
     n_tau = len(case.tau)
     stream = torch.cuda.current_stream()
     ctx = Context(local, stream)
+    if args.batch_atoms > 0:
+        ctx.set_option("batch_atoms", args.batch_atoms)
     ctx.load_case(case)
     nri = ctx.nri
     out = torch.empty((1, nri, nri), dtype=torch.float64, device=f"cuda:{local}")
@@ -347,8 +349,10 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16x6": "bf16x6",
                                        "fp16x3": "f16x3", "fp64": "f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": "armchair-ribbon-298 (200 C + 98 H, 3090 AO / 7176 RI, "
-                               "20 tau in [0.01, 50] a.u., thr 1e-9)",
+        "config": {"workload": ("armchair-ribbon-298 (200 C + 98 H, 3090 AO / 7176 RI, "
+                                "20 tau in [0.01, 50] a.u., thr 1e-9)") if args.workload == WORKLOAD
+                   else f"{case.system.name} ({case.system.nao_total} AO / "
+                        f"{case.system.nri_total} RI, {len(case.tau)} tau, thr {case.thr:g})",
                    "form": prec, "l2": "inputs and per-step operands larger than L2 (11 GB 3c)",
                    "parallelism": f"tau-sharded replicas x{world}"},
         "roofline": roof,
@@ -444,6 +448,10 @@ def main():
     ap.add_argument("--fp64-taus", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=1)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic case (smaller ones serve profiling); the bench line is %(default)s")
+    ap.add_argument("--batch-atoms", type=int, default=0,
+                    help="upper limit on sigma-atoms per operand batch (0: byte budget only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

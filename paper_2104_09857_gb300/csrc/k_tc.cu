@@ -1142,7 +1142,8 @@ void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long
   tc::k_slices_block_flags<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
       ri_off, rowoff, pa0, npa, n_at, ns, thr, norm2, blockflag, tileflag, ntile, tile_rows, zlist,
       zcount);
-  tc::k_slices_zero_blocks<<<152 * 4, 256, 0, st>>>(static_cast<uint16_t*>(Z), slices, slice_elems, ldk,
+  // many warps: each queued block is a few kilobytes of scattered rows
+  tc::k_slices_zero_blocks<<<152 * 64, 256, 0, st>>>(static_cast<uint16_t*>(Z), slices, slice_elems, ldk,
                                                   rowoff, ri_off, ao_off, n_ao, s0, seg, pa0, npa, n_at,
                                                   zlist, zcount);
 }

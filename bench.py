@@ -105,6 +105,27 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def tau_index(i: int, world: int, rank: int, n_tau: int) -> int:
+    """tau point of step i on rank `rank`: the ranks take interleaved points of
+    the tau cycle (independent problems, no exchange)."""
+    return (i * world + rank) % n_tau
+
+
+def job_totals(t_local: float, flops_local: float, device) -> tuple[float, float]:
+    """Whole-job time (max over ranks) and useful flops (sum over ranks); the
+    local values when no process group of more than one rank is running."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, flops_local
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ff = torch.tensor([flops_local], dtype=torch.float64, device=device)
+    dist.all_reduce(ff, op=dist.ReduceOp.SUM)
+    return tt.item(), ff.item()
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,7 +312,7 @@ def run_ours(args):
 
     # warm-up (W steps on the first tau points of this rank's cycle)
     for w in range(args.warmup):
-        step((w * world + rank) % n_tau, prec)
+        step(tau_index(w, world, rank, n_tau), prec)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -305,7 +326,7 @@ def run_ours(args):
            "flops_issued": 0.0, "c_launches": 0, "ms_step_ab": 0.0, "ms_greens": 0.0,
            "flops_a": 0.0, "flops_b": 0.0, "n_batches": 0}
     for i in range(args.steps):
-        st = step((i * world + rank) % n_tau, prec)
+        st = step(tau_index(i, world, rank, n_tau), prec)
         for k in agg:
             agg[k] += st[k]
     ev1.record(stream)
@@ -314,19 +335,9 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     t_local = ms / 1e3
     flops_local = agg["flops_useful"]
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([t_local], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ff = torch.tensor([flops_local], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(ff, op=dist.ReduceOp.SUM)
-        t_job, flops_job = tt.item(), ff.item()
-    else:
-        t_job, flops_job = t_local, flops_local
+    t_job, flops_job = job_totals(t_local, flops_local, f"cuda:{local}")
     value = flops_job / t_job / 1e12
-    ms_per_tau = t_job * 1e3 * world / max(1, args.steps * world) if world else 0.0
-    ms_per_tau = t_job * 1e3 / max(1, args.steps)
+    ms_per_tau = t_job * 1e3 / max(1, args.steps)  # per tau point on one GPU
 
     # rooflines of the two tensor-core kernels: steps A/B (k_tc_persistent
     # PanelJob, two launches per batch) and step C (ChiJob, one per batch);

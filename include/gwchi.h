@@ -239,6 +239,13 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *   "c_order"      with c_split_k = 0: tile order, 0 longest first (default),
  *                  1 grouped raster
  *   "mlp_margin"   learned screening: decades added to the predicted norm
+ * Fault-injection hooks for tests (no effect on results when 0):
+ *   "test_fail_alloc"  1: the next new device work buffer fails to allocate
+ *                      (the call returns GW_ERR_OOM; the hook then clears)
+ *   "test_stall_tc"    1: in gw_chi_tau, every tensor-core kernel waits first
+ *                      on a dependency that is never met; its bounded waits
+ *                      expire after about 2 s and the call returns
+ *                      GW_ERR_TIMEOUT (the context stays usable)
  * Unknown keys and out-of-range values return GW_ERR_INVALID_ARG.            */
 int gw_set_option(gw_ctx* ctx, const char* key, double value);
 

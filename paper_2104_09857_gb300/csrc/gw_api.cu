@@ -75,6 +75,12 @@ int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
     wb.erase(it);
   }
   void* p = nullptr;
+  if (bytes > 0 && ctx->test_fail_alloc) {
+    ctx->test_fail_alloc = 0;
+    ctx->err = std::string("cudaMalloc of work buffer '") + name + "' (" + std::to_string(bytes) +
+               " bytes): injected failure (option test_fail_alloc)";
+    return GW_ERR_OOM;
+  }
   if (bytes > 0) {
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
@@ -1328,6 +1334,14 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->batch_bytes = value;
     return GW_OK;
   }
+  if (!strcmp(key, "test_fail_alloc")) {
+    ctx->test_fail_alloc = value != 0.0;
+    return GW_OK;
+  }
+  if (!strcmp(key, "test_stall_tc")) {
+    ctx->test_stall = value != 0.0;
+    return GW_OK;
+  }
   if (!strcmp(key, "c_split_k")) {
     if (!(value >= 0 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "c_split_k must be in [0, 2^30]");
     ctx->c_split_k = (int)value;
@@ -1419,6 +1433,11 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   ctx->mlp_skipped = ctx->mlp_seen = 0;
   ctx->mlp_k_before = ctx->mlp_k_after = 0.0;
   auto t_start = std::chrono::steady_clock::now();
+  // test hook "test_stall_tc", on for this call only
+  struct StallScope {
+    explicit StallScope(int on) { gw::tc_set_stall_test(on); }
+    ~StallScope() { gw::tc_set_stall_test(0); }
+  } stall_scope(ctx->test_stall);
   int rc;
   if ((rc = build_panels(ctx, thr))) return rc;
   const bool f64 = precision == GW_FP64;

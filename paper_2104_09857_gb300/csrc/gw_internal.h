@@ -186,5 +186,9 @@ struct gw_ctx {
   // elements, FP64 atomics into chi (0: whole tiles, bitwise reproducible)
   int c_split_k = 2048;
 
+  // test hooks (options "test_fail_alloc", "test_stall_tc")
+  int test_fail_alloc = 0;  // the next new work-buffer allocation fails
+  int test_stall = 0;       // tensor-core kernels wait on a dependency never met
+
   gw_stats stats{};
 };

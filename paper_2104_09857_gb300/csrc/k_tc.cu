@@ -221,6 +221,7 @@ __device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
 // main drains.
 struct Cadence {
   int main, small_every, write_every;
+  int stall;  // test hook: the epilogue first waits on a barrier nothing arrives at
 };
 
 // Per-epilogue-warp staging: 32 rows x kStgCols floats, row pitch
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* small_full = main_empty + kMainBufs;  // the small accumulator
   uint64_t* small_empty = small_full + 1;
   uint64_t* drain = small_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // arrived at by nothing (stall test hook)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
 
@@ -563,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(small_full, 1);
     mbar_init(small_empty, kEpiWarps);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -714,7 +717,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0);
     float acc[kEpiCols];
     int chunk = 0, schunk = 0;
-    bool ok = true;
+    // test hook: a dependency that is never satisfied; the bounded wait
+    // gives up and the kernel reports a time-out instead of hanging
+    bool ok = cad.stall ? mbar_wait(never, 0, abort_flag) : true;
     for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
       const typename Job::Tile T = job.tile(t);
       const long long n = job.nsteps(T);
@@ -1004,6 +1009,8 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+int g_stall_test = 0;
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -1037,6 +1044,7 @@ template <class Job>
 int launch_persistent(int slices, int f16, const CUtensorMap& ma, const CUtensorMap& mb, const Job& job,
                       int flush_k, int* err_flag, cudaStream_t st) {
   tc::Cadence cad;
+  cad.stall = g_stall_test;
   cad.main = flush_k / tc::kMmaK > 0 ? flush_k / tc::kMmaK : 1;
   const int fk = cad.main * tc::kMmaK;
   cad.small_every = tc::kSmallK / fk > 0 ? tc::kSmallK / fk : 1;
@@ -1070,6 +1078,8 @@ int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long lon
 }
 
 int tc_tile_rows() { return tc::kTileM; }
+
+void tc_set_stall_test(int on) { g_stall_test = on; }
 
 int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, const CUtensorMap& my,
                   const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,

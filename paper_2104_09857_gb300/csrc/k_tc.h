@@ -20,6 +20,10 @@ int make_slice_map(CUtensorMap* map, const void* base, long long k_len, long lon
                    int box_rows, int f16);
 // Rows (and columns) of one step-C tile of the tensor-core kernel.
 int tc_tile_rows();
+// Test hook (process-wide): while on, every tensor-core kernel launched has
+// its epilogue wait first on a barrier that nothing arrives at, so that the
+// bounded waits expire (about 2 s) and the kernel returns its error flag.
+void tc_set_stall_test(int on);
 // 2^(14 - ceil(log2 bound)): scales a value of magnitude <= bound to <= 2^14
 // (1 for a zero or non-finite bound).
 double pow2_scale(double bound);

@@ -1,0 +1,62 @@
+"""Failure detection without a GPU fault: an injected never-met dependency in
+the tensor-core kernels comes back as GW_ERR_TIMEOUT (bounded waits, about 2 s)
+and an injected work-buffer allocation failure as GW_ERR_OOM; in both cases
+the same context then computes chi correctly."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import chi as oc  # noqa: E402
+from synth import make_case  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_09857_gb300 as p
+
+    return p
+
+
+def _rel(got, ref):
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(got, ref))
+
+
+def test_injected_stall_times_out_and_context_recovers(pkg):
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("benzene", n_tau=2)
+    ref = oc.chi_dense(case)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        ctx.set_option("test_stall_tc", 1)
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_tau(case.thr, "fp16x3", 0, 1)
+        assert e.value.code == -7  # GW_ERR_TIMEOUT
+        ctx.set_option("test_stall_tc", 0)
+        got = ctx.chi_tau(case.thr, "fp16x3").cpu().numpy()
+    assert _rel(got, ref) <= 1e-6
+
+
+def test_injected_allocation_failure_and_context_recovers(pkg):
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("benzene", n_tau=2)
+    ref = oc.chi_dense(case)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        ctx.set_option("test_fail_alloc", 1)
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_tau(case.thr, "fp64")
+        assert e.value.code == -5  # GW_ERR_OOM
+        assert "injected" in str(e.value)
+        got = ctx.chi_tau(case.thr, "fp64").cpu().numpy()
+    assert _rel(got, ref) <= 1e-10

@@ -935,6 +935,57 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       fc_scale = (ctx->mlp_k_after - ka0) / (ctx->mlp_k_before - kb0);
     ctx->stats.kernel_launches += 4;
   }
+  CUtensorMap mx, my;
+  if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile, f16) ||
+      gw::make_slice_map(&my, ys, Kb, nri, slices, tile, f16))
+    return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
+  cudaEvent_t ec0, ec1;
+  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
+  const double fc_scale_dev = fc_scale;
+  if (ctx->c_split_k > 0 && !ctx->mlp_mode) {
+    // step-C work units planned on the device: no host synchronisation; the
+    // task statistics are read at the end of the tau point
+    const int ntiles = npt * nqt;
+    const size_t cap = std::max<size_t>((size_t)ntiles * nslab, 1);
+    gw::UnitScratch w{};
+    unsigned long long* tstat;
+    if ((rc = wsT(ctx, "u_ucnt", std::max(ntiles, 1), &w.ucnt)) ||
+        (rc = wsT(ctx, "u_uoff", std::max(ntiles, 1), &w.uoff)) ||
+        (rc = wsT(ctx, "u_ttile", cap, &w.t_tile)) || (rc = wsT(ctx, "u_tfirst", cap, &w.t_first)) ||
+        (rc = wsT(ctx, "u_tcount", cap, &w.t_count)) || (rc = wsT(ctx, "u_tkey", cap, &w.t_key)) ||
+        (rc = wsT(ctx, "u_tile", cap, &w.u_tile)) || (rc = wsT(ctx, "u_first", cap, &w.u_first)) ||
+        (rc = wsT(ctx, "u_count", cap, &w.u_count)) ||
+        (rc = wsT(ctx, "u_hist", std::max(nslab, 1), &w.hist)) ||
+        (rc = wsT(ctx, "u_start", std::max(nslab, 1), &w.start)) ||
+        (rc = wsT(ctx, "u_nunits", 1, &w.n_units)) || (rc = wsT(ctx, "u_nkeys", 1, &w.total_keys)) ||
+        (rc = wsT(ctx, "task_stats", 3, &tstat)))
+      return rc;
+    gw::launch_plan_units(tasks, counts, kacc, d_len, ntiles, nslab, ctx->c_split_k, w, tstat,
+                          ctx->stream);
+    GW_CHECK_LAUNCH();
+    ctx->stats.kernel_launches += 5;
+    ctx->tc_issue_per_k = 2.0 * tile * tile * prods;
+    GW_TRY(cudaEventRecord(ec0, ctx->stream));
+    if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, w.u_tile, w.u_first,
+                                w.u_count, (int)std::min<size_t>(cap, INT32_MAX), w.n_units, tasks,
+                                counts, nslab, d_k0, d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k,
+                                d_err, ctx->stream))
+      return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
+    GW_CHECK_LAUNCH();
+    GW_TRY(cudaEventRecord(ec1, ctx->stream));
+    ctx->stats.c_launches += 1;
+    ctx->stats.kernel_launches += 1;
+    double* d_fc_all;
+    if ((rc = wsT(ctx, "fc_all", (size_t)n_at * n_at, &d_fc_all))) return rc;
+    GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * n_at * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * n_at, fc_scale_dev});
+    ctx->tc_fc_used += (long long)ns * n_at;
+    ctx->stats.tiles_total += (long long)ntiles;
+    ctx->stats.slabs_total += (long long)ntiles * nslab;
+    ctx->stats.flops_issued += issued;
+    return GW_OK;
+  }
   std::vector<int> h_counts((size_t)npt * nqt);
   std::vector<long long> h_kacc((size_t)npt * nqt);
   GW_TRY(cudaMemcpyAsync(h_counts.data(), counts, h_counts.size() * sizeof(int),
@@ -960,12 +1011,6 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     std::stable_sort(active.begin(), active.end(),
                      [&](int a, int c) { return h_kacc[a] > h_kacc[c]; });
   }
-  CUtensorMap mx, my;
-  if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile, f16) ||
-      gw::make_slice_map(&my, ys, Kb, nri, slices, tile, f16))
-    return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
-  cudaEvent_t ec0, ec1;
-  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
   if (ctx->c_split_k > 0) {
     // split every tile's list into units of about c_split_k reduction
     // elements
@@ -1017,7 +1062,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     if ((rc = upload(ctx, "unit_count", u_count, &d_uc))) return rc;
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_ut, d_uf, d_uc,
-                                (int)u_tile.size(), tasks, counts,
+                                (int)u_tile.size(), nullptr, tasks, counts,
                                 nslab, d_k0, d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err,
                                 ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
@@ -1067,8 +1112,12 @@ int tc_begin_tau(gw_ctx* ctx) {
   if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
   if ((rc = wsT(ctx, "fc_all", (size_t)ctx->n_at * ctx->n_at, &d_fc_all))) return rc;
   GW_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+  unsigned long long* tstat;
+  if ((rc = wsT(ctx, "task_stats", 3, &tstat))) return rc;
+  GW_TRY(cudaMemsetAsync(tstat, 0, 3 * sizeof(unsigned long long), ctx->stream));
   ctx->tc_pending.clear();
   ctx->tc_fc_used = 0;
+  ctx->tc_issue_per_k = 0.0;
   return GW_OK;
 }
 
@@ -1088,6 +1137,14 @@ int tc_finish_tau(gw_ctx* ctx, std::vector<double>& fc_host) {
   std::vector<double> h_fc((size_t)ctx->tc_fc_used);
   if (!h_fc.empty())
     GW_TRY(cudaMemcpy(h_fc.data(), d_fc_all, h_fc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  // task statistics of the batches whose units were planned on the device
+  unsigned long long* tstat;
+  unsigned long long h_stat[3] = {0, 0, 0};
+  if ((rc = wsT(ctx, "task_stats", 3, &tstat))) return rc;
+  GW_TRY(cudaMemcpy(h_stat, tstat, sizeof(h_stat), cudaMemcpyDeviceToHost));
+  ctx->stats.tiles_active += (long long)h_stat[0];
+  ctx->stats.slabs_active += (long long)h_stat[1];
+  ctx->stats.flops_issued += ctx->tc_issue_per_k * (double)h_stat[2];
   for (const auto& p : ctx->tc_pending) {
     cudaEvent_t ec0, ec1, ea0, ea1;
     if ((rc = c_event_pair(ctx, p.batch_idx, &ec0, &ec1))) return rc;

@@ -155,6 +155,7 @@ struct gw_ctx {
   };
   std::vector<TcPending> tc_pending;
   long long tc_fc_used = 0;
+  double tc_issue_per_k = 0.0;  // issued flops per reduction element of a step-C tile
   bool ycov_valid = false;  // cleared whenever the panels are rebuilt
   bool ycov_ok = false;
   int* d_ycov_lo = nullptr;

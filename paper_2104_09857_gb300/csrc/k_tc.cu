@@ -256,6 +256,7 @@ struct ChiJob {
   int nqt, P0, prow, nri;
   double* chi;
   float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
+  const int* n_dev; // optional: number of units in device memory (n_tiles = capacity)
   static constexpr bool kPeriodic = true;
   static constexpr int kDrainHalves = 2;  // 96 registers: one 32-column load would spill
 
@@ -282,6 +283,7 @@ struct ChiJob {
     for (int i = 0; i < T.cnt; ++i) n += slab_len[T.list[i]] / kStageK;
     return n;
   }
+  __device__ int items() const { return n_dev ? *n_dev : n_tiles; }
   struct Iter {
     const ChiJob* j;
     const int* list;
@@ -423,6 +425,7 @@ struct PanelJob {
     return T;
   }
   __device__ long long nsteps(const Tile& T) const { return T.ksteps; }
+  __device__ int items() const { return n_tiles; }
   struct Iter {
     int x;
     __device__ void init(const PanelJob*, const Tile&) { x = 0; }
@@ -579,6 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int n_items = job.items();  // work items (tiles or units) of the launch
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool armed[kStages];
       for (int s = 0; s < kStages; ++s) armed[s] = false, armed_parity[s] = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
+      for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
         typename Job::Iter it;
@@ -633,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int chunk = 0, schunk = 0;
       bool ok = true, issued_any = false;
-      for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
+      for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
         const long long nsub = n * kSub;
@@ -720,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // test hook: a dependency that is never satisfied; the bounded wait
     // gives up and the kernel reports a time-out instead of hanging
     bool ok = cad.stall ? mbar_wait(never, 0, abort_flag) : true;
-    for (int t = blockIdx.x; t < job.n_tiles && ok; t += gridDim.x) {
+    for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
       const typename Job::Tile T = job.tile(t);
       const long long n = job.nsteps(T);
       const long long nch = (n * kSub + cad.main - 1) / cad.main;
@@ -929,6 +933,110 @@ __global__ void k_split_f64(const double* __restrict__ a, long long ld, int rows
   }
 }
 
+// ---------------------------------------------------------------------------
+// step-C work units planned on the device
+// ---------------------------------------------------------------------------
+// A tile's slab list is cut into units: consecutive slabs until at least
+// split reduction elements (the last unit takes the rest).  One thread per
+// tile counts its units and adds the tile to the task statistics
+// (stat[0] active tiles, stat[1] listed slabs, stat[2] reduction elements).
+__global__ void k_units_count(const int* __restrict__ tasks, const int* __restrict__ counts,
+                              const long long* __restrict__ kacc, const int* __restrict__ slab_len,
+                              int ntiles, int nslab, int split, int* __restrict__ ucnt,
+                              unsigned long long* __restrict__ stat) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    const int c = counts[t];
+    const int* lst = tasks + static_cast<long long>(t) * nslab;
+    int nu = 0;
+    long long kk = 0;
+    for (int i = 0; i < c; ++i) {
+      kk += slab_len[lst[i]];
+      if (kk >= split || i == c - 1) {
+        ++nu;
+        kk = 0;
+      }
+    }
+    ucnt[t] = nu;
+    if (c > 0) {
+      atomicAdd(stat, 1ull);
+      atomicAdd(stat + 1, static_cast<unsigned long long>(c));
+      atomicAdd(stat + 2, static_cast<unsigned long long>(kacc[t]));
+    }
+  }
+}
+
+// Exclusive scan of v[0..n) into out[0..n) with one CTA of 1024 threads;
+// *total = the sum.  Optionally zeroes zero[0..nz).
+__global__ void k_scan_1cta(const int* __restrict__ v, int n, int* __restrict__ out,
+                            int* __restrict__ total, int* __restrict__ zero, int nz) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) zero[i] = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int x = i < n ? v[i] : 0;
+    part[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {  // inclusive Hillis-Steele scan
+      const int y = threadIdx.x >= static_cast<unsigned>(o) ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + part[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// One thread per tile writes its units at uoff[t] with the key of each (its
+// first slab) and counts the keys.
+__global__ void k_units_emit(const int* __restrict__ tasks, const int* __restrict__ counts,
+                             const int* __restrict__ slab_len, int ntiles, int nslab, int split,
+                             const int* __restrict__ uoff, int* __restrict__ t_tile,
+                             int* __restrict__ t_first, int* __restrict__ t_count,
+                             int* __restrict__ t_key, int* __restrict__ hist) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    const int c = counts[t];
+    const int* lst = tasks + static_cast<long long>(t) * nslab;
+    int u = uoff[t], i0 = 0;
+    long long kk = 0;
+    for (int i = 0; i < c; ++i) {
+      kk += slab_len[lst[i]];
+      if (kk >= split || i == c - 1) {
+        t_tile[u] = t;
+        t_first[u] = i0;
+        t_count[u] = i + 1 - i0;
+        t_key[u] = lst[i0];
+        atomicAdd(hist + lst[i0], 1);
+        ++u;
+        i0 = i + 1;
+        kk = 0;
+      }
+    }
+  }
+}
+
+// Units in order of their key (first slab, i.e. first reduction index):
+// start[k] = first position of key k, advanced atomically.
+__global__ void k_units_scatter(const int* __restrict__ n_units, const int* __restrict__ t_tile,
+                                const int* __restrict__ t_first, const int* __restrict__ t_count,
+                                const int* __restrict__ t_key, int* __restrict__ start,
+                                int* __restrict__ u_tile, int* __restrict__ u_first,
+                                int* __restrict__ u_count) {
+  const int n = *n_units;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const int pos = atomicAdd(start + t_key[u], 1);
+    u_tile[pos] = t_tile[u];
+    u_first[pos] = t_first[u];
+    u_count[pos] = t_count[u];
+  }
+}
+
 // out[0] = max |a|, out[1] = max over rows of sum |a[r][:]| (out zeroed by
 // the caller): non-negative doubles order like their bit patterns.
 __global__ void k_absmax_rowsum(const double* __restrict__ a, long long ld, int rows, int cols,
@@ -968,6 +1076,23 @@ double pow2_scale(double bound) {
   if (!(bound > 0.0) || !std::isfinite(bound)) return 1.0;
   // the scaled bound is at most 2^14: four times below the binary16 maximum
   return std::ldexp(1.0, 14 - static_cast<int>(std::ceil(std::log2(bound))));
+}
+
+void launch_plan_units(const int* tasks, const int* counts, const long long* kacc, const int* slab_len,
+                       int ntiles, int nslab, int split, UnitScratch w, unsigned long long* stat,
+                       cudaStream_t st) {
+  if (ntiles == 0) {
+    cudaMemsetAsync(w.n_units, 0, sizeof(int), st);
+    return;
+  }
+  const int g = (ntiles + 255) / 256;
+  tc::k_units_count<<<g, 256, 0, st>>>(tasks, counts, kacc, slab_len, ntiles, nslab, split, w.ucnt, stat);
+  tc::k_scan_1cta<<<1, 1024, 0, st>>>(w.ucnt, ntiles, w.uoff, w.n_units, w.hist, nslab);
+  tc::k_units_emit<<<g, 256, 0, st>>>(tasks, counts, slab_len, ntiles, nslab, split, w.uoff, w.t_tile,
+                                      w.t_first, w.t_count, w.t_key, w.hist);
+  tc::k_scan_1cta<<<1, 1024, 0, st>>>(w.hist, nslab, w.start, w.total_keys, nullptr, 0);
+  tc::k_units_scatter<<<152 * 4, 256, 0, st>>>(w.n_units, w.t_tile, w.t_first, w.t_count, w.t_key,
+                                               w.start, w.u_tile, w.u_first, w.u_count);
 }
 
 void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int nri, int ns,
@@ -1086,17 +1211,18 @@ int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, c
                   const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
                   double* chi, int flush_k, int* err_flag, cudaStream_t st) {
   tc::ChiJob job{tile_list, n_tiles, nullptr, nullptr, tasks, counts, max_slab, slab_k0, slab_len, nqt,
-                 P0, prow, nri, chi, out_scale};
+                 P0, prow, nri, chi, out_scale, nullptr};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
 int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap& mx,
                         const CUtensorMap& my, const int* unit_tile, const int* unit_first,
-                        const int* unit_count, int n_units, const int* tasks, const int* counts,
-                        int max_slab, const long long* slab_k0, const int* slab_len, int P0, int prow,
-                        int nri, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st) {
+                        const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
+                        const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
+                        int P0, int prow, int nri, int nqt, double* chi, int flush_k, int* err_flag,
+                        cudaStream_t st) {
   tc::ChiJob job{unit_tile, n_units, unit_first, unit_count, tasks, counts, max_slab, slab_k0, slab_len,
-                 nqt, P0, prow, nri, chi, out_scale};
+                 nqt, P0, prow, nri, chi, out_scale, n_units_dev};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 

@@ -42,12 +42,31 @@ int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, c
                   double* chi, int flush_k, int* err_flag, cudaStream_t st);
 // Step C over work units that split tiles along K: unit u computes tile
 // unit_tile[u] over list entries [unit_first[u], unit_first[u] + unit_count[u])
-// of that tile's task list and adds into chi with FP64 atomics.
+// of that tile's task list and adds into chi with FP64 atomics.  The number
+// of units is n_units, or *n_units_dev (device memory) when that is not null,
+// n_units then being the capacity of the unit arrays.
 int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap& mx,
                         const CUtensorMap& my, const int* unit_tile, const int* unit_first,
-                        const int* unit_count, int n_units, const int* tasks, const int* counts,
-                        int max_slab, const long long* slab_k0, const int* slab_len, int P0, int prow,
-                        int nri, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st);
+                        const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
+                        const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
+                        int P0, int prow, int nri, int nqt, double* chi, int flush_k, int* err_flag,
+                        cudaStream_t st);
+// Device scratch of launch_plan_units: per tile (ntiles) ucnt, uoff; per unit
+// (capacity ntiles * nslab) t_tile, t_first, t_count, t_key, u_tile, u_first,
+// u_count; per slab (nslab) hist, start; and the counters n_units,
+// total_keys.
+struct UnitScratch {
+  int *ucnt, *uoff, *t_tile, *t_first, *t_count, *t_key, *u_tile, *u_first, *u_count, *hist, *start;
+  int *n_units, *total_keys;
+};
+// Step-C work units planned on the device from the task lists: tiles cut
+// into units of at least `split` reduction elements (the last of a tile
+// takes the rest), ordered by first slab (first reduction index); counts in
+// *w.n_units.  Adds the active tiles, listed slabs and reduction elements
+// into stat[0..2].
+void launch_plan_units(const int* tasks, const int* counts, const long long* kacc, const int* slab_len,
+                       int ntiles, int nslab, int split, UnitScratch w, unsigned long long* stat,
+                       cudaStream_t st);
 // Steps A/B on the tensor cores (PanelJob in k_tc.cu): mode 0 writes X, mode
 // 1 writes Y, as slices of out_scale * (unscale * accumulator), and
 // accumulates the squared atom-block norms of unscale * accumulator.  Tile

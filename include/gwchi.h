@@ -120,8 +120,25 @@ int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
  * norm is < thr is dropped (thr = 0: nothing is dropped, exact zeros are still
  * skipped).  chi is formed on atom blocks atom(P) <= atom(Q) and mirrored.
  *
+ * precision (enum gw_precision): GW_FP64 and GW_FP32 on the CUDA cores;
+ * GW_BF16X3, GW_BF16X6 and GW_FP16X3 as split 16-bit products on the tensor
+ * cores with FP64 accumulation of chi across work units.  screening:
+ * GW_SCREEN_BOUND (the exact filter above) or GW_SCREEN_MLP (tensor-core forms
+ * only, after gw_mlp_init/gw_mlp_train: step-C tasks the network predicts
+ * below thr are skipped as well).
+ *
+ * Reproducibility: FP64, FP32 and the tensor-core forms with option
+ * c_split_k = 0 give bitwise identical results run to run; with the default
+ * split-K work units the tensor-core forms add into chi with FP64 atomics,
+ * so the last bits can vary.
+ *
  * chi_out: [tau_count][n_ri_total][n_ri_total] FP64, a device pointer if
- * out_on_device != 0, else a host pointer. */
+ * out_on_device != 0, else a host pointer.  Work buffers are allocated on the
+ * device and kept in the context between calls (released by gw_destroy).
+ * Errors: GW_ERR_ORDER (inputs missing), GW_ERR_INVALID_ARG (range, thr,
+ * precision), GW_ERR_UNSUPPORTED (learned screening with a CUDA-core form),
+ * GW_ERR_OOM, GW_ERR_CUDA, GW_ERR_TIMEOUT (a bounded wait of a tensor-core
+ * kernel gave up; the context stays usable). */
 int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision,
                int screening, double* chi_out, int out_on_device);
 

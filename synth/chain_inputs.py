@@ -11,6 +11,8 @@ the synthetic Coulomb matrix of the auxiliary basis.
 * delta[j][k] (i omega -> tau): least-squares weights with
       sum_k delta_jk 2x / (x^2 + omega_k^2) ~= exp(-x tau_j)
   over the same x.
+* s[k][j] (half-line sine transform, for the self-energy): least-squares
+  weights with sum_j s_kj exp(-x tau_j) ~= omega_k / (x^2 + omega_k^2).
 * V_PQ = 1 / sqrt(r_PQ^2 + 1 A^2) + 1.0 delta_PQ over the RI-function centres:
   a regularised Coulomb kernel (positive Fourier transform, hence positive
   semidefinite) plus a diagonal shift, so V is symmetric positive definite.
@@ -53,6 +55,25 @@ def fit_error(tau, omega, gamma, delta, gap, width) -> tuple[float, float]:
     eg = np.abs(e @ gamma.T - f).max() / np.abs(f).max()
     ed = np.abs(f @ delta.T - e).max() / np.abs(e).max()
     return float(eg), float(ed)
+
+
+def sine_weights(tau: np.ndarray, omega: np.ndarray, gap: float, width: float) -> np.ndarray:
+    """s [n_omega, n_tau]: least-squares weights of the half-line sine
+    transform, sum_j s_kj exp(-x tau_j) ~= omega_k / (x^2 + omega_k^2), for x
+    on the same log grid over [gap, width] (the half-line cosine weights are
+    gamma / 2)."""
+    x = _x_samples(gap, width)
+    e = np.exp(-np.outer(x, tau))
+    f = omega[None, :] / (x[:, None] ** 2 + omega[None, :] ** 2)
+    return np.ascontiguousarray(np.linalg.lstsq(e, f, rcond=1e-14)[0].T)
+
+
+def sine_fit_error(tau, omega, s, gap, width) -> float:
+    """Max relative error of the fitted sine transform over the x range."""
+    x = _x_samples(gap, width, 997)
+    e = np.exp(-np.outer(x, tau))
+    f = omega[None, :] / (x[:, None] ** 2 + omega[None, :] ** 2)
+    return float(np.abs(e @ s.T - f).max() / np.abs(f).max())
 
 
 def coulomb_matrix(system) -> np.ndarray:

@@ -237,6 +237,30 @@ int gw_mlp_train(gw_ctx* ctx, const float* feat, const float* target, long long 
                  long long batch, float lr, unsigned long long seed, float* loss_per_epoch);
 int gw_mlp_predict(gw_ctx* ctx, const float* feat, long long n, float* pred);
 
+/* G0W0 quasiparticle energies, Eq. 12, FP64 on the device, from the diagonal
+ * self-energy on imaginary time (the output layout of gw_sigma_tau):
+ *   Sigma^c_n(i omega_k) = sum_j [gamma_kj / 2 (S+_j + S-_j) - i s_kj (S+_j - S-_j)]
+ * with S+_j = sigma_c[a][j][0] = Sigma^c_n(i tau_j), S-_j = sigma_c[a][j][1]
+ * = Sigma^c_n(-i tau_j) (the sine and cosine transform of the paper's
+ * quasiparticle step, Fourier kernel e^{-i omega tau}); gamma [n_omega][n_tau]
+ * are full-line cosine weights (those of gw_chi_to_w; gamma/2 is the
+ * half-line transform) and s_weights [n_omega][n_tau] half-line sine weights.
+ * Sigma^c_n is continued to the real axis by a Pade interpolant through the
+ * n_omega points i omega_k (Thiele continued fraction, Vidberg-Serene
+ * coefficients) and
+ *   e = eps[a] - vxc[a] + sx[a] + Re Sigma^c_n(e)
+ * is solved by Newton-Raphson from eps[a] (derivative of Re Sigma^c by
+ * central differences, step 1e-6; |step| < 1e-12 max(1, |e|); at most 100
+ * iterations, count in iters_out[a] if not NULL).  sx is the exchange term
+ * of Eq. 11 and vxc the mean-field exchange-correlation level.  All arrays
+ * are host memory; 2 <= n_omega <= 128, omega positive and distinct
+ * (GW_ERR_INVALID_ARG), finite inputs (GW_ERR_NONFINITE).  Independent of the
+ * context's basis and tensor. */
+int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const double* sigma_c,
+               const double* omega, const double* gamma, const double* s_weights,
+               const double* eps, const double* vxc, const double* sx, double* qp_out,
+               int* iters_out);
+
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
 

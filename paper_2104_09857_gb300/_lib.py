@@ -89,6 +89,7 @@ SIGNATURES = [
     ("gw_chi_tau_noalloc", _I, [_P, _I, _D, _P]),
     ("gw_chi_to_w", _I, [_P, _P, _I, _P, _P, _P, _I, _P, _I]),
     ("gw_sigma_tau", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
+    ("gw_qp_g0w0", _I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("gw_mlp_log", _I, [_P, _I, _I, _D, _I, _P, _P, _LL, ctypes.POINTER(_LL)]),
     ("gw_mlp_init", _I, [_P, ctypes.c_ulonglong]),
     ("gw_mlp_set_params", _I, [_P, _P, _LL]),
@@ -201,6 +202,22 @@ def gw_sigma_tau(ctx: int, w_ptr: int, w_on_device: bool, orbitals, n_tau: int, 
     _check(ctx, lib().gw_sigma_tau(ctx, w_ptr, int(bool(w_on_device)), _ptr(orbitals), orbitals.size,
                                    float(thr), int(precision), _ptr(out)))
     return out
+
+
+def gw_qp_g0w0(ctx: int, sigma_c, omega, gamma, s_weights, eps, vxc, sx):
+    """(quasiparticle energies [n_orb], Newton iterations [n_orb]) from
+    sigma_c [n_orb, n_tau, 2] (the layout of gw_sigma_tau)."""
+    sig = np.ascontiguousarray(sigma_c, dtype=np.float64)
+    n_orb, n_tau = sig.shape[0], sig.shape[1]
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    sw = np.ascontiguousarray(s_weights, dtype=np.float64)
+    e, v, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (eps, vxc, sx))
+    out = np.zeros(n_orb)
+    it = np.zeros(n_orb, dtype=np.int32)
+    _check(ctx, lib().gw_qp_g0w0(ctx, n_orb, n_tau, om.size, _ptr(sig), _ptr(om), _ptr(g), _ptr(sw),
+                                 _ptr(e), _ptr(v), _ptr(x), _ptr(out), _ptr(it)))
+    return out, it
 
 
 def gw_mlp_log(ctx: int, tau_first: int, tau_count: int, thr: float, precision: int,

@@ -237,6 +237,16 @@ int gw_mlp_train(gw_ctx* ctx, const float* feat, const float* target, long long 
                  long long batch, float lr, unsigned long long seed, float* loss_per_epoch);
 int gw_mlp_predict(gw_ctx* ctx, const float* feat, long long n, float* pred);
 
+/* Static exchange self-energy of Eq. 11 for the orbitals listed, with the RI
+ * metric S = 1:
+ *   Sigma^x_n = - sum_{mu nu} D_{mu nu} sum_{PQ} B^n_{mu P} V_PQ B^n_{nu Q},
+ *   D = sum_{i occ} C_mu,i C_nu,i  (the density matrix, G^occ at tau = 0)
+ * computed by the engine of gw_sigma_tau with W = V at tau = 0.  V[n_ri][n_ri]:
+ * device if v_on_device else host.  Filter and precision as gw_sigma_tau.
+ * sx_out: host, [n_orb]. */
+int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const int* orbitals, int n_orb,
+               double thr, int precision, double* sx_out);
+
 /* G0W0 quasiparticle energies, Eq. 12, FP64 on the device, from the diagonal
  * self-energy on imaginary time (the output layout of gw_sigma_tau):
  *   Sigma^c_n(i omega_k) = sum_j [gamma_kj / 2 (S+_j + S-_j) - i s_kj (S+_j - S-_j)]

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("gw_chi_to_w", _I, [_P, _P, _I, _P, _P, _P, _I, _P, _I]),
     ("gw_sigma_tau", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
     ("gw_qp_g0w0", _I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    ("gw_sigma_x", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
     ("gw_mlp_log", _I, [_P, _I, _I, _D, _I, _P, _P, _LL, ctypes.POINTER(_LL)]),
     ("gw_mlp_init", _I, [_P, ctypes.c_ulonglong]),
     ("gw_mlp_set_params", _I, [_P, _P, _LL]),
@@ -201,6 +202,16 @@ def gw_sigma_tau(ctx: int, w_ptr: int, w_on_device: bool, orbitals, n_tau: int, 
     out = np.zeros((orbitals.size, n_tau, 2))
     _check(ctx, lib().gw_sigma_tau(ctx, w_ptr, int(bool(w_on_device)), _ptr(orbitals), orbitals.size,
                                    float(thr), int(precision), _ptr(out)))
+    return out
+
+
+def gw_sigma_x(ctx: int, v, orbitals, thr: float, precision: int = GW_FP64) -> np.ndarray:
+    """Sigma^x_n (Eq. 11) [n_orb] for the orbitals; v: host [n_ri, n_ri]."""
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    orbitals = np.ascontiguousarray(orbitals, dtype=np.int32)
+    out = np.zeros(orbitals.size)
+    _check(ctx, lib().gw_sigma_x(ctx, _ptr(vv), 0, _ptr(orbitals), orbitals.size, float(thr),
+                                 int(precision), _ptr(out)))
     return out
 
 

@@ -106,10 +106,11 @@ struct DevBuf {
 constexpr int kDotBlocks = 256;
 }  // namespace
 
-extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
-                            int n_orb, double thr, int precision, double* sigma_out) {
-  if (!ctx) return GW_ERR_INVALID_ARG;
-  ctx->err.clear();
+namespace {
+// Eq. 10 for the listed orbitals at the imaginary times taus[0..n_tau), with
+// W_tau[n_tau][n_ri][n_ri]; sigma_out [n_orb][n_tau][2] = (-S^occ, +S^virt).
+int sigma_impl(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals, int n_orb,
+               double thr, int precision, const double* taus, int n_tau, double* sigma_out) {
   if (ctx->n_at == 0 || ctx->blk_off.empty() || !ctx->have_greens) {
     ctx->err = "gw_sigma_tau: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
     return GW_ERR_ORDER;
@@ -127,7 +128,7 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
   const bool mixed = precision != GW_FP64;
   const int slices = precision == GW_BF16X6 ? 3 : 2;
   const int f16 = precision == GW_FP16X3;
-  const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at, n_tau = (int)ctx->tau.size();
+  const int nao = ctx->nao, nri = ctx->nri, n_at = ctx->n_at;
   for (int a = 0; a < n_orb; ++a)
     if (orbitals[a] < 0 || orbitals[a] >= nao) {
       ctx->err = "gw_sigma_tau: orbital index out of range";
@@ -251,7 +252,7 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
     m_bq = m_b;
   }
   for (int jt = 0; jt < n_tau; ++jt) {
-    gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[jt], (double*)b_cso.p,
+    gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, taus[jt], (double*)b_cso.p,
                       (double*)b_csv.p, go, gv, st);
     if (thr > 0.0) {
       gw::launch_sym_block_filter(go, nao, ctx->d_ao_off, n_at, thr, (unsigned char*)b_fl.p, st);
@@ -321,5 +322,40 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
       return GW_ERR_TIMEOUT;
     }
   }
+  return GW_OK;
+}
+}  // namespace
+
+extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
+                            int n_orb, double thr, int precision, double* sigma_out) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->have_greens) {
+    ctx->err = "gw_sigma_tau: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
+    return GW_ERR_ORDER;
+  }
+  return sigma_impl(ctx, W_tau, w_on_device, orbitals, n_orb, thr, precision, ctx->tau.data(),
+                    (int)ctx->tau.size(), sigma_out);
+}
+
+// Eq. 11 is Eq. 10's contraction with W = V at tau = 0, where G^occ(0) is the
+// density matrix D = C_occ C_occ^T: Sigma^x_n = -S^occ_n.
+extern "C" int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const int* orbitals,
+                          int n_orb, double thr, int precision, double* sx_out) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->have_greens) {
+    ctx->err = "gw_sigma_x: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
+    return GW_ERR_ORDER;
+  }
+  if (!sx_out || n_orb <= 0 || n_orb > 1024) {
+    ctx->err = "gw_sigma_x: bad arguments";
+    return GW_ERR_INVALID_ARG;
+  }
+  const double tau0 = 0.0;
+  std::vector<double> tmp((size_t)n_orb * 2);
+  const int rc = sigma_impl(ctx, V, v_on_device, orbitals, n_orb, thr, precision, &tau0, 1, tmp.data());
+  if (rc) return rc;
+  for (int a = 0; a < n_orb; ++a) sx_out[a] = tmp[(size_t)a * 2];
   return GW_OK;
 }

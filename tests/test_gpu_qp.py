@@ -97,3 +97,19 @@ def test_qp_rejects_bad_input(pkg):
         with pytest.raises(_lib.GwError) as e:
             _lib.gw_qp_g0w0(ctx.ctx, sig, [0.1, 0.2, 0.5], w, w, [np.nan], [0.0], [0.0])
         assert e.value.code == -4
+
+
+@pytest.mark.parametrize("name,precision,tol", [("benzene", "fp64", 1e-10), ("ribbon28", "fp64", 1e-10),
+                                                ("ribbon28", "fp16x3", 1e-6)])
+def test_sigma_x_matches_oracle(pkg, name, precision, tol):
+    """Eq. 11 through gw_sigma_x against the oracle's dense route."""
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case(name, n_tau=2)
+    _, _, _, v, _, _ = chain_inputs(case)
+    orbs = [case.n_occ - 2, case.n_occ - 1, case.n_occ]
+    ref = qp.sigma_x_dense(case, v, orbs, thr=case.thr)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        got = _lib.gw_sigma_x(ctx.ctx, v, orbs, case.thr, _lib.PRECISIONS[precision])
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))

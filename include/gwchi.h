@@ -237,6 +237,15 @@ int gw_mlp_train(gw_ctx* ctx, const float* feat, const float* target, long long 
                  long long batch, float lr, unsigned long long seed, float* loss_per_epoch);
 int gw_mlp_predict(gw_ctx* ctx, const float* feat, long long n, float* pred);
 
+/* RI metric of Eqs. 5, 10 and 11: out[k] = S^-1 M[k] S^-1 for n_mat symmetric
+ * [n_ri][n_ri] matrices (chi~ = S^-1 chi S^-1 before gw_chi_to_w, W~ before
+ * gw_sigma_tau, V~ before gw_sigma_x), FP64 on the device through the
+ * Cholesky factor S = R R^T.  S: host [n_ri][n_ri], symmetric positive
+ * definite (GW_ERR_NOT_SPD otherwise).  M and out: device or host as flagged;
+ * out may not alias M. */
+int gw_ri_metric(gw_ctx* ctx, const double* S, int n_mat, const double* M, int m_on_device,
+                 double* out, int out_on_device);
+
 /* Static exchange self-energy of Eq. 11 for the orbitals listed, with the RI
  * metric S = 1:
  *   Sigma^x_n = - sum_{mu nu} D_{mu nu} sum_{PQ} B^n_{mu P} V_PQ B^n_{nu Q},

@@ -8,7 +8,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Readings:
 * The RI overlap metric S is the identity for the synthetic inputs (the
-  tilde quantities of Eqs. 5-6 equal the plain ones).
+  tilde quantities of Eqs. 5-6 equal the plain ones); apply_metric forms
+  S^-1 M S^-1 for a general symmetric positive definite S (chi~ of Eq. 5,
+  W~ of Eq. 10, V~ of Eq. 11).
 * chi here is real and negative semidefinite (chi^0 / i); eps = 1 - L^T chi L
   is then >= 1 and positive definite, as the paper requires of it.
 * The transform weights gamma (tau -> omega) and delta (omega -> tau) are
@@ -89,3 +91,12 @@ def chi_omega_closed_form(t: np.ndarray, C: np.ndarray, eps: np.ndarray, n_occ: 
     w = 2.0 * d / (d * d + omega * omega)
     nb = b.shape[0] * b.shape[1]
     return -((b * w[:, :, None]).reshape(nb, -1).T @ b.reshape(nb, -1))
+
+
+def apply_metric(s: np.ndarray, m: np.ndarray) -> np.ndarray:
+    """S^-1 M S^-1 (Eq. 5 and the tilde quantities of Eqs. 10-11) through the
+    Cholesky factor S = R R^T: S^-1 = R^-T R^-1."""
+    r = cholesky_lower(s)
+    rinv = solve_lower(r, np.eye(s.shape[0]))
+    sinv = rinv.T @ rinv
+    return sinv @ m @ sinv

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("gw_sigma_tau", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
     ("gw_qp_g0w0", _I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("gw_sigma_x", _I, [_P, _P, _I, _P, _I, _D, _I, _P]),
+    ("gw_ri_metric", _I, [_P, _P, _I, _P, _I, _P, _I]),
     ("gw_mlp_log", _I, [_P, _I, _I, _D, _I, _P, _P, _LL, ctypes.POINTER(_LL)]),
     ("gw_mlp_init", _I, [_P, ctypes.c_ulonglong]),
     ("gw_mlp_set_params", _I, [_P, _P, _LL]),
@@ -203,6 +204,18 @@ def gw_sigma_tau(ctx: int, w_ptr: int, w_on_device: bool, orbitals, n_tau: int, 
     _check(ctx, lib().gw_sigma_tau(ctx, w_ptr, int(bool(w_on_device)), _ptr(orbitals), orbitals.size,
                                    float(thr), int(precision), _ptr(out)))
     return out
+
+
+def gw_ri_metric(ctx: int, s, m) -> np.ndarray:
+    """S^-1 M[k] S^-1 for host matrices m [n_mat, n_ri, n_ri] (or one matrix)."""
+    ss = np.ascontiguousarray(s, dtype=np.float64)
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    one = mm.ndim == 2
+    if one:
+        mm = mm[None]
+    out = np.zeros_like(mm)
+    _check(ctx, lib().gw_ri_metric(ctx, _ptr(ss), mm.shape[0], _ptr(mm), 0, _ptr(out), 0))
+    return out[0] if one else out
 
 
 def gw_sigma_x(ctx: int, v, orbitals, thr: float, precision: int = GW_FP64) -> np.ndarray:

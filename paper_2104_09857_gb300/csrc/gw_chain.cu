@@ -22,7 +22,7 @@ struct DevBuf {
   do {                                                                            \
     cudaError_t e_ = (call);                                                      \
     if (e_ != cudaSuccess) {                                                      \
-      ctx->err = std::string("gw_chi_to_w: ") + #call + ": " + cudaGetErrorString(e_); \
+      ctx->err = std::string("chain: ") + #call + ": " + cudaGetErrorString(e_);      \
       return e_ == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA;          \
     }                                                                             \
   } while (0)
@@ -131,5 +131,73 @@ extern "C" int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const doub
     ctx->err = "gw_chi_to_w: eps(i omega) is not positive definite (chi must be negative semidefinite)";
     return GW_ERR_NOT_SPD;
   }
+  return GW_OK;
+}
+
+// S^-1 M S^-1 for n_mat symmetric matrices M (chi~ of Eq. 5, W~ of Eq. 10,
+// V~ of Eq. 11), FP64: S = R R^T (blocked Cholesky), R^-1 by a triangular
+// solve on the identity, S^-1 = R^-T R^-1, then two products per matrix.
+extern "C" int gw_ri_metric(gw_ctx* ctx, const double* S, int n_mat, const double* M, int m_on_device,
+                            double* out, int out_on_device) {
+  if (!ctx) return GW_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_at == 0) {
+    ctx->err = "gw_ri_metric: call gw_set_basis first (the RI size)";
+    return GW_ERR_ORDER;
+  }
+  if (!S || !M || !out || n_mat <= 0) {
+    ctx->err = "gw_ri_metric: bad arguments";
+    return GW_ERR_INVALID_ARG;
+  }
+  const int n = ctx->nri;
+  const size_t nn = (size_t)n * n;
+  for (size_t i = 0; i < nn; ++i)
+    if (!std::isfinite(S[i])) {
+      ctx->err = "gw_ri_metric: non-finite metric element";
+      return GW_ERR_NONFINITE;
+    }
+  CH_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  DevBuf b_r, b_ri, b_si, b_t, b_m, b_o, b_err;
+  CH_TRY(cudaMalloc(&b_r.p, nn * 8));
+  CH_TRY(cudaMalloc(&b_ri.p, nn * 8));
+  CH_TRY(cudaMalloc(&b_si.p, nn * 8));
+  CH_TRY(cudaMalloc(&b_t.p, nn * 8));
+  CH_TRY(cudaMalloc(&b_err.p, sizeof(int)));
+  double *r = (double*)b_r.p, *ri = (double*)b_ri.p, *si = (double*)b_si.p, *t = (double*)b_t.p;
+  int* err = (int*)b_err.p;
+  const double* m = M;
+  if (!m_on_device) {
+    CH_TRY(cudaMalloc(&b_m.p, (size_t)n_mat * nn * 8));
+    CH_TRY(cudaMemcpyAsync(b_m.p, M, (size_t)n_mat * nn * 8, cudaMemcpyHostToDevice, st));
+    m = (const double*)b_m.p;
+  }
+  double* o = out;
+  if (!out_on_device) {
+    CH_TRY(cudaMalloc(&b_o.p, (size_t)n_mat * nn * 8));
+    o = (double*)b_o.p;
+  }
+  CH_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  CH_TRY(cudaMemcpyAsync(r, S, nn * 8, cudaMemcpyHostToDevice, st));
+  gw::chain_potrf(r, n, err, st);
+  CH_TRY(cudaGetLastError());
+  int h_err = 0;
+  CH_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CH_TRY(cudaStreamSynchronize(st));
+  if (h_err) {
+    ctx->err = "gw_ri_metric: the metric is not positive definite";
+    return GW_ERR_NOT_SPD;
+  }
+  gw::chain_set_identity(ri, n, st);
+  gw::chain_trsm_left_lower(r, n, ri, n, st);                                 // R^-1
+  gw::chain_dgemm(true, false, n, n, n, 1.0, ri, n, ri, n, 0.0, si, n, st);  // S^-1 = R^-T R^-1
+  for (int k = 0; k < n_mat; ++k) {
+    gw::chain_dgemm(false, false, n, n, n, 1.0, si, n, m + (size_t)k * nn, n, 0.0, t, n, st);
+    gw::chain_dgemm(false, false, n, n, n, 1.0, t, n, si, n, 0.0, o + (size_t)k * nn, n, st);
+  }
+  CH_TRY(cudaGetLastError());
+  if (!out_on_device)
+    CH_TRY(cudaMemcpyAsync(out, o, (size_t)n_mat * nn * 8, cudaMemcpyDeviceToHost, st));
+  CH_TRY(cudaStreamSynchronize(st));
   return GW_OK;
 }

@@ -76,3 +76,35 @@ def test_chain_rejects_non_spd(pkg):
         with pytest.raises(_lib.GwError) as e:
             ctx.chi_to_w(-1e6 * chi, v, gamma, delta)
         assert e.value.code == -8
+
+
+def test_ri_metric_matches_oracle(pkg):
+    """S^-1 M S^-1 on the GPU against the oracle for a random SPD metric of
+    the benzene RI size; the identity metric returns M; an indefinite metric
+    is refused with GW_ERR_NOT_SPD."""
+    from oracle import chain as och
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("benzene", n_tau=2)
+    n = case.system.nri_total
+    rng = np.random.default_rng(21)
+    b = rng.standard_normal((n, n))
+    s = b @ b.T / n + np.eye(n)
+    ms = []
+    for _ in range(3):
+        a = rng.standard_normal((n, n))
+        ms.append(a + a.T)
+    ms = np.stack(ms)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        got = _lib.gw_ri_metric(ctx.ctx, s, ms)
+        same = _lib.gw_ri_metric(ctx.ctx, np.eye(n), ms[0])
+        bad = np.eye(n)
+        bad[3, 3] = -1.0
+        with pytest.raises(_lib.GwError) as e:
+            _lib.gw_ri_metric(ctx.ctx, bad, ms[0])
+        assert e.value.code == -8
+    for k in range(3):
+        ref = och.apply_metric(s, ms[k])
+        assert np.abs(got[k] - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(same - ms[0]).max() <= 1e-14 * np.abs(ms[0]).max()

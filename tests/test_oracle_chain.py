@@ -92,3 +92,22 @@ def test_chain_end_to_end_shapes_and_sign(benzene):
     # every W^c(i omega) is negative semidefinite
     for w in w_w:
         assert np.linalg.eigvalsh(0.5 * (w + w.T)).max() <= 1e-10 * np.abs(w).max()
+
+
+def test_apply_metric_pins():
+    """S^-1 M S^-1: identity metric, diagonal metric in closed form, and the
+    defining equation S X S = M for a random SPD metric."""
+    from oracle import chain as och
+
+    rng = np.random.default_rng(11)
+    n = 24
+    a = rng.standard_normal((n, n))
+    m = a + a.T
+    assert np.allclose(och.apply_metric(np.eye(n), m), m, rtol=0, atol=1e-13)
+    d = rng.uniform(0.5, 2.0, n)
+    assert np.allclose(och.apply_metric(np.diag(d), m), m / np.outer(d, d), rtol=1e-12, atol=0)
+    b = rng.standard_normal((n, n))
+    s = b @ b.T / n + np.eye(n)
+    x = och.apply_metric(s, m)
+    assert np.allclose(s @ x @ s, m, rtol=0, atol=1e-10 * np.abs(m).max())
+    assert np.allclose(x, x.T, rtol=0, atol=1e-12 * np.abs(x).max())

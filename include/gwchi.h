@@ -10,6 +10,10 @@
  * library creates).  Host arrays passed in are copied before the call returns;
  * the library never keeps or frees caller memory.
  *
+ * Threads: all state (device buffers, events, options, errors) belongs to a
+ * context, so separate contexts may be driven from separate host threads at
+ * the same time.  One context must not be used by two threads at once.
+ *
  * Units: distances in Angstrom, energies in Hartree, imaginary time in a.u.
  * Layouts are row-major.  Atom-blocked basis: atom a owns n_ao[a] consecutive
  * primary (AO) functions and n_ri[a] consecutive auxiliary (RI) functions, in

@@ -31,13 +31,6 @@ using gw::PanelTask;
 
 namespace {
 
-struct WorkBufs {
-  std::map<std::string, std::pair<void*, size_t>> m;
-};
-std::map<const gw_ctx*, WorkBufs>& work_registry() {
-  static std::map<const gw_ctx*, WorkBufs> r;
-  return r;
-}
 
 #define GW_TRY(call)                                                                  \
   do {                                                                                \
@@ -64,7 +57,7 @@ int fail(gw_ctx* ctx, int code, const std::string& msg) {
 
 // named device scratch buffer, grown on demand
 int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
-  auto& wb = work_registry()[ctx].m;
+  auto& wb = ctx->work;
   auto it = wb.find(name);
   if (it != wb.end() && it->second.second >= bytes) {
     *out = it->second.first;
@@ -98,7 +91,7 @@ int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
 // release every scratch buffer of a context (before a route with different
 // buffer sizes, so that two routes' operands are never resident together)
 void ws_release_all(gw_ctx* ctx) {
-  auto& wb = work_registry()[ctx].m;
+  auto& wb = ctx->work;
   if (wb.empty()) return;
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : wb) cudaFree(kv.second.first);
@@ -361,14 +354,10 @@ std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_by
   return out;
 }
 
-// CUDA events bracketing each step-C launch (reused across calls)
-std::vector<cudaEvent_t>& c_events(const gw_ctx* ctx) {
-  static std::map<const gw_ctx*, std::vector<cudaEvent_t>> m;
-  return m[ctx];
-}
-
+// CUDA events bracketing the step launches of each batch (two pairs per
+// batch: 2 b for step C, 2 b + 1 for steps A/B), kept in the context
 int c_event_pair(gw_ctx* ctx, size_t idx, cudaEvent_t* a, cudaEvent_t* b) {
-  auto& v = c_events(ctx);
+  auto& v = ctx->events;
   while (v.size() < 2 * (idx + 1)) {
     cudaEvent_t e;
     GW_TRY(cudaEventCreate(&e));
@@ -524,7 +513,7 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
 
   // step C
   cudaEvent_t ec0, ec1;
-  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
+  if ((rc = c_event_pair(ctx, 2 * batch_idx, &ec0, &ec1))) return rc;
   std::vector<int> h_counts((size_t)npt * nqt);
   int* d_err = nullptr;
   {
@@ -740,7 +729,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
   double issued = 0.0;
   cudaEvent_t ea0, ea1;
-  if ((rc = c_event_pair(ctx, (size_t{1} << 20) + batch_idx, &ea0, &ea1))) return rc;
+  if ((rc = c_event_pair(ctx, 2 * batch_idx + 1, &ea0, &ea1))) return rc;
   GW_TRY(cudaEventRecord(ea0, ctx->stream));
 
   // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu ----
@@ -940,7 +929,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       gw::make_slice_map(&my, ys, Kb, nri, slices, tile, f16))
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
   cudaEvent_t ec0, ec1;
-  if ((rc = c_event_pair(ctx, batch_idx, &ec0, &ec1))) return rc;
+  if ((rc = c_event_pair(ctx, 2 * batch_idx, &ec0, &ec1))) return rc;
   const double fc_scale_dev = fc_scale;
   if (ctx->c_split_k > 0 && !ctx->mlp_mode) {
     // step-C work units planned on the device: no host synchronisation; the
@@ -1147,8 +1136,8 @@ int tc_finish_tau(gw_ctx* ctx, std::vector<double>& fc_host) {
   ctx->stats.flops_issued += ctx->tc_issue_per_k * (double)h_stat[2];
   for (const auto& p : ctx->tc_pending) {
     cudaEvent_t ec0, ec1, ea0, ea1;
-    if ((rc = c_event_pair(ctx, p.batch_idx, &ec0, &ec1))) return rc;
-    if ((rc = c_event_pair(ctx, (size_t{1} << 20) + p.batch_idx, &ea0, &ea1))) return rc;
+    if ((rc = c_event_pair(ctx, 2 * p.batch_idx, &ec0, &ec1))) return rc;
+    if ((rc = c_event_pair(ctx, 2 * p.batch_idx + 1, &ea0, &ea1))) return rc;
     float ms_ck = 0.f, ms_ab = 0.f;
     GW_TRY(cudaEventElapsedTime(&ms_ck, ec0, ec1));
     GW_TRY(cudaEventElapsedTime(&ms_ab, ea0, ea1));
@@ -1215,14 +1204,10 @@ void gw_destroy(gw_ctx* ctx) {
   free_dev(ctx->d_mlp_v);
   free_dev(ctx->d_ycov_lo);
   free_dev(ctx->d_ycov_hi);
-  for (cudaEvent_t e : c_events(ctx)) cudaEventDestroy(e);
-  c_events(ctx).clear();
-  auto& reg = work_registry();
-  auto it = reg.find(ctx);
-  if (it != reg.end()) {
-    for (auto& kv : it->second.m) free_dev(kv.second.first);
-    reg.erase(it);
-  }
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  ctx->events.clear();
+  for (auto& kv : ctx->work) free_dev(kv.second.first);
+  ctx->work.clear();
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

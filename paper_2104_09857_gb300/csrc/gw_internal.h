@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/gwchi.h"
@@ -186,6 +188,11 @@ struct gw_ctx {
   // step-C work units: tiles split into runs of about c_split_k reduction
   // elements, FP64 atomics into chi (0: whole tiles, bitwise reproducible)
   int c_split_k = 2048;
+
+  // named device work buffers (grown on demand) and the step timing events
+  // of this context; a context is used by one host thread at a time
+  std::map<std::string, std::pair<void*, size_t>> work;
+  std::vector<cudaEvent_t> events;
 
   // test hooks (options "test_fail_alloc", "test_stall_tc")
   int test_fail_alloc = 0;  // the next new work-buffer allocation fails

@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "gw_internal.h"
@@ -1122,29 +1123,29 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // resolved once per process (a function-local static is initialised once,
+  // even under concurrent first calls)
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return EncodeTiledFn{nullptr};
+  }();
   return fn;
 }
 
-int g_stall_test = 0;
+thread_local int g_stall_test = 0;  // test hook, per host thread
 
+// SM count of the current device (queried per call: contexts of one process
+// may sit on different devices)
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
 }
 
 template <int S, class Job, bool F16>
@@ -1152,12 +1153,17 @@ int launch_persistent_t(const CUtensorMap& ma, const CUtensorMap& mb, const Job&
                         int* err_flag, cudaStream_t st) {
   if (job.n_tiles == 0) return 0;
   constexpr int smem = tc::Smem<S>::kTotal;
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory opt-in is a per-device attribute of the kernel; setting
+  // it twice (two threads racing on a first launch) is harmless
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
     if (cudaFuncSetAttribute(tc::k_tc_persistent<S, Job, F16>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
-    attr = true;
+    attr_set.fetch_or(bit, std::memory_order_release);
   }
   const int grid = job.n_tiles < num_sms() ? job.n_tiles : num_sms();
   tc::k_tc_persistent<S, Job, F16><<<grid, tc::kThreads, smem, st>>>(ma, mb, job, cad, err_flag);

@@ -1,0 +1,134 @@
+"""Pins of the minimax-grid oracle (oracle/grids.py) against what fixes a best
+approximation independently of how it was computed: the equioscillation
+(alternation) characterisation on a fine grid, brute force for one term,
+local optimality under perturbation, monotonicity in n and R, the half-line
+limit, and the scaling to physical energies."""
+
+import numpy as np
+import pytest
+
+from oracle import grids as og
+
+CASES = [("T", 1, 10.0), ("T", 4, 7.66), ("T", 6, 7.66), ("T", 8, 100.0), ("T", 12, 1e3),
+         ("F", 1, 10.0), ("F", 4, 7.66), ("F", 8, 100.0), ("F", 12, 1e3)]
+
+
+@pytest.fixture(scope="module")
+def solved():
+    with np.errstate(all="ignore"):
+        return {c: og.minimax_unit(*c) for c in CASES}
+
+
+def _fine(R, m=40001):
+    return np.exp(np.linspace(0.0, np.log(R), m))
+
+
+def _alternations(e, level):
+    """Longest run of alternating signs among the points where |e| reaches
+    `level` (consecutive same-sign points count once)."""
+    s = np.sign(e[np.abs(e) >= level])
+    if len(s) == 0:
+        return 0, 0
+    runs = [s[0]]
+    for v in s[1:]:
+        if v != runs[-1]:
+            runs.append(v)
+    return len(runs), runs[0]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}{c[1]}_R{c[2]:g}")
+def test_error_equioscillates_at_2n_plus_1_points(solved, case):
+    """Chebyshev's characterisation: the best n-term approximation (2n
+    parameters) has an error of constant modulus E at 2n + 1 points of
+    alternating sign, positive at both ends; any other approximant with that
+    property would have the same E (de la Vallee Poussin)."""
+    kind, n, R = case
+    p, a, E = solved[case]
+    x = _fine(R)
+    e = og.error(kind, x, a, p)
+    assert np.abs(e).max() == pytest.approx(E, rel=1e-6)
+    count, first = _alternations(e, (1.0 - 1e-5) * E)
+    assert count >= 2 * n + 1
+    assert first > 0
+    assert np.all(a > 0) and np.all(p > 0) and np.all(np.diff(p) > 0)
+
+
+def _brute_one_term(kind, R):
+    """min over (a, p) of max |1/x - a b(x; p)| by a nested grid search."""
+    x = _fine(R, 4001)
+    lo_a, hi_a, lo_p, hi_p = 0.05, 5.0, 0.02, 5.0
+    best = (np.inf, 0, 0)
+    for _ in range(6):
+        A = np.linspace(lo_a, hi_a, 161)
+        P = np.linspace(lo_p, hi_p, 161)
+        B = og.basis(kind, x, P)                                    # [x, p]
+        err = np.abs(1.0 / x[:, None, None] - A[None, :, None] * B[:, None, :]).max(axis=0)
+        i, j = np.unravel_index(np.argmin(err), err.shape)
+        best = (err[i, j], A[i], P[j])
+        da, dp = 4 * (A[1] - A[0]), 4 * (P[1] - P[0])
+        lo_a, hi_a = max(1e-3, A[i] - da), A[i] + da
+        lo_p, hi_p = max(1e-3, P[j] - dp), P[j] + dp
+    return best
+
+
+@pytest.mark.parametrize("kind", ["T", "F"])
+def test_one_term_matches_brute_force(solved, kind):
+    p, a, E = solved[(kind, 1, 10.0)]
+    e_brute, a_b, p_b = _brute_one_term(kind, 10.0)
+    # the search's best pair, measured on the same fine grid as E
+    e_brute = np.abs(og.error(kind, _fine(10.0), np.array([a_b]), np.array([p_b]))).max()
+    assert E <= e_brute * (1 + 1e-9)
+    assert E == pytest.approx(e_brute, rel=2e-4)
+    assert a[0] == pytest.approx(a_b, rel=1e-2)
+    assert p[0] == pytest.approx(p_b, rel=1e-2)
+
+
+@pytest.mark.parametrize("case", [("T", 6, 7.66), ("F", 8, 100.0)], ids=["T6", "F8"])
+def test_no_nearby_parameters_do_better(solved, case):
+    """Small random perturbations of the 2n parameters never lower the
+    maximum error (local optimality in the max norm)."""
+    kind, n, R = case
+    p, a, E = solved[case]
+    x = _fine(R, 20001)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        s = 10.0 ** rng.uniform(-9, -5)
+        ap = a * (1 + s * rng.standard_normal(n))
+        pp = p * (1 + s * rng.standard_normal(n))
+        assert np.abs(og.error(kind, x, ap, pp)).max() >= E * (1 - 1e-9)
+
+
+def test_error_falls_with_n_and_grows_with_R(solved):
+    with np.errstate(all="ignore"):
+        for kind in ("T", "F"):
+            e4 = og.minimax_unit(kind, 4, 100.0)[2]
+            assert solved[(kind, 8, 100.0)][2] < e4
+            e = [og.minimax_unit(kind, 4, R)[2] for R in (5.0, 20.0, 80.0)]
+            assert e[0] < e[1] < e[2]
+
+
+def test_half_line_limit():
+    """One term: the half-line solution has its last alternation point near
+    x = 12; beyond that R no longer matters."""
+    with np.errstate(all="ignore"):
+        r1 = og.minimax_unit("T", 1, 1e3)
+        r2 = og.minimax_unit("T", 1, 1e6)
+    assert r1[2] == pytest.approx(r2[2], rel=1e-9)
+    assert r1[0][0] == pytest.approx(r2[0][0], rel=1e-6)
+
+
+@pytest.mark.parametrize("kind", ["T", "F"])
+def test_physical_grid_bounds_the_energy_denominator(kind):
+    """The physical grid approximates 1/E for every E in [e_min, e_max]
+    within the returned error, which is attained."""
+    e_min, e_max = 0.3, 2.3
+    with np.errstate(all="ignore"):
+        nodes, w, err = og.minimax_grid(kind, 5, e_min, e_max)
+    E = np.linspace(e_min, e_max, 20001)
+    if kind == "T":
+        approx = np.exp(-np.outer(E, nodes)) @ w
+    else:
+        approx = (E[:, None] ** 2 / (E[:, None] ** 2 + nodes[None, :] ** 2) ** 2) @ w
+    dev = np.abs(1.0 / E - approx)
+    assert dev.max() <= err * (1 + 1e-6)
+    assert dev.max() >= err * (1 - 1e-4)

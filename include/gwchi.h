@@ -41,7 +41,8 @@ enum gw_status {
   GW_ERR_CUDA = -6,        /* a CUDA runtime call or kernel failed           */
   GW_ERR_TIMEOUT = -7,     /* a bounded device wait gave up                  */
   GW_ERR_NOT_SPD = -8,     /* a Cholesky factorisation met a non-positive pivot */
-  GW_ERR_UNSUPPORTED = -9  /* option not available in this build             */
+  GW_ERR_UNSUPPORTED = -9, /* option not available in this build             */
+  GW_ERR_NOT_CONVERGED = -10 /* an iterative host solve did not converge       */
 };
 
 /* Arithmetic of the contraction steps (Eq. 3).  Green's functions are always
@@ -283,6 +284,29 @@ int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const double* sig
                const double* omega, const double* gamma, const double* s_weights,
                const double* eps, const double* vxc, const double* sx, double* qp_out,
                int* iters_out);
+
+/* Minimax grids of the imaginary-time / imaginary-frequency method (the grids
+ * chi is computed on and cosine-transformed over; the passage before Eq. 7
+ * and the Computational Details).  With transition energies E in
+ * [e_min, e_max], x = E / e_min and R = e_max / e_min, the grid is the n-term
+ * best approximation of 1/x on [1, R] in the maximum norm:
+ *   GW_GRID_TIME: 1/E ~ sum_j weights[j] exp(-nodes[j] E)
+ *                 (nodes = tau_j in a.u., from 1/E = int_0^inf e^{-E t} dt)
+ *   GW_GRID_FREQ: 1/E ~ sum_k weights[k] E^2 / (E^2 + nodes[k]^2)^2
+ *                 (nodes = omega_k, from 1/E = 4/pi int_0^inf E^2/(E^2+w^2)^2 dw)
+ * Its error equioscillates at 2n + 1 energies; *max_err = max |1/E - sum| over
+ * [e_min, e_max].  nodes ascending, weights positive.  Host code only: needs
+ * no context and no GPU; thread-safe.  nodes, weights: caller arrays of n
+ * doubles.  Errors: GW_ERR_INVALID_ARG (kind, 1 <= n <= GW_GRID_MAX_N,
+ * 0 < e_min, e_max > e_min (1 + 1e-9), null pointers), GW_ERR_NONFINITE,
+ * GW_ERR_NOT_CONVERGED where the best error falls to the FP64 rounding level
+ * (about 1e-10 relative to 1/e_min: fewer points suffice there).  Remez
+ * exchange with Levenberg-Marquardt levelling; about a millisecond to a
+ * second depending on n and R. */
+enum gw_grid_kind { GW_GRID_TIME = 0, GW_GRID_FREQ = 1 };
+#define GW_GRID_MAX_N 64
+int gw_minimax_grid(int kind, int n, double e_min, double e_max, double* nodes, double* weights,
+                    double* max_err);
 
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);

@@ -29,7 +29,10 @@ ERRORS = {
     -7: "GW_ERR_TIMEOUT",
     -8: "GW_ERR_NOT_SPD",
     -9: "GW_ERR_UNSUPPORTED",
+    -10: "GW_ERR_NOT_CONVERGED",
 }
+GW_GRID_TIME, GW_GRID_FREQ = 0, 1
+GW_GRID_MAX_N = 64
 
 PRECISIONS = {"fp64": GW_FP64, "fp32": GW_FP32, "bf16x3": GW_BF16X3, "bf16x6": GW_BF16X6,
               "fp16x3": GW_FP16X3}
@@ -99,6 +102,7 @@ SIGNATURES = [
     ("gw_mlp_grad", _I, [_P, _P, _P, _LL, _P, _P]),
     ("gw_mlp_train", _I, [_P, _P, _P, _LL, _I, _LL, ctypes.c_float, ctypes.c_ulonglong, _P]),
     ("gw_mlp_predict", _I, [_P, _P, _LL, _P]),
+    ("gw_minimax_grid", _I, [_I, _I, _D, _D, _P, _P, ctypes.POINTER(_D)]),
 ]
 
 MLP_FEATURES = 8
@@ -141,6 +145,20 @@ def _check(ctx, rc: int) -> None:
 # ---------------------------------------------------------------------------
 # thin functions with the C names
 # ---------------------------------------------------------------------------
+
+def gw_minimax_grid(kind: int, n: int, e_min: float, e_max: float):
+    """(nodes [n], weights [n], max_err) of the minimax time (GW_GRID_TIME) or
+    frequency (GW_GRID_FREQ) grid for transition energies in [e_min, e_max].
+    Host code: needs no context and no GPU."""
+    nodes = np.zeros(max(n, 1), np.float64)
+    weights = np.zeros(max(n, 1), np.float64)
+    err = _D(0.0)
+    rc = lib().gw_minimax_grid(int(kind), int(n), float(e_min), float(e_max), _ptr(nodes),
+                               _ptr(weights), ctypes.byref(err))
+    if rc != GW_OK:
+        raise GwError(rc, "gw_minimax_grid")
+    return nodes[:n], weights[:n], err.value
+
 
 def gw_create(device: int = 0, stream: int | None = None) -> int:
     out = _P()

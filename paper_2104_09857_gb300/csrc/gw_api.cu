@@ -370,7 +370,7 @@ int c_event_pair(gw_ctx* ctx, size_t idx, cudaEvent_t* a, cudaEvent_t* b) {
 
 template <typename T>
 int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, const T* pool,
-                  double thr, double* acc, std::vector<double>& fc_host, int precision,
+                  double thr, double* acc, std::vector<double>& fc_host, int /*precision*/,
                   size_t batch_idx) {
   const int ns = b.s1 - b.s0;
   const int prow = b.P1 - b.P0;
@@ -1499,7 +1499,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
       plan_batches(ctx, esz, ctx->batch_bytes, tcpath ? gw::tc_tile_rows() : 0);
   ctx->stats.n_batches = (int)batches.size();
 
-  double *cso, *csv, *go, *gv, *acc, *stage;
+  double *cso, *csv, *go, *gv, *acc, *stage = nullptr;
   float *go32 = nullptr, *gv32 = nullptr;
   unsigned char *flo, *flv;
   if ((rc = wsT(ctx, "cso", (size_t)nao * std::max(ctx->n_occ, 1), &cso))) return rc;

@@ -111,8 +111,11 @@ int gw_set_3c_tensor(gw_ctx* ctx, long long n_blocks, const int* blk_abp,
 
 /* Mean-field orbitals and the imaginary-time grid of Eq. 2.
  * C[n_ao_total * n_ao_total]: column n is orbital n (C[mu*n_ao_total + n] is the
- * paper's C_{n mu}); eps[n_ao_total] ascending; orbitals 0..n_occ-1 occupied;
- * mu_fermi the energy zero of the exponentials; tau[n_tau] > 0. */
+ * paper's C_{n mu}); eps[n_ao_total] the orbital energies (ascending as a rule;
+ * the order is not used); orbitals 0..n_occ-1 occupied; mu_fermi the energy
+ * zero of the exponentials, which decay only if every occupied level lies
+ * below it and every virtual level above (not checked); tau[n_tau] > 0.
+ * Minimax tau points come from gw_minimax_grid. */
 int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ,
                   double mu_fermi, const double* tau, int n_tau);
 
@@ -307,6 +310,28 @@ enum gw_grid_kind { GW_GRID_TIME = 0, GW_GRID_FREQ = 1 };
 #define GW_GRID_MAX_N 64
 int gw_minimax_grid(int kind, int n, double e_min, double e_max, double* nodes, double* weights,
                     double* max_err);
+
+/* Weights of the transforms between imaginary time and frequency, for the
+ * tau grid tau[n_tau] and frequency grid omega[n_omega] (both > 0) and
+ * transition energies in [e_min, e_max] (the cosine transform before Eq. 7
+ * and its inverse after Eq. 9; the sine and cosine transform of Sigma^c in
+ * the quasiparticle step).  Least squares over 400 energies x log-spaced on
+ * [e_min, e_max], minimum-norm solution with singular values below 1e-14 of
+ * the largest dropped (one-sided Jacobi SVD):
+ *   gamma[n_omega][n_tau]:  sum_j gamma_kj e^{-x tau_j}           ~ 2x/(x^2+omega_k^2)
+ *   delta[n_tau][n_omega]:  sum_k delta_jk 2x/(x^2+omega_k^2)    ~ e^{-x tau_j}
+ *   s_weights[n_omega][n_tau]: sum_j s_kj e^{-x tau_j}           ~ omega_k/(x^2+omega_k^2)
+ * gamma and delta are the inputs of gw_chi_to_w; gamma and s_weights those of
+ * gw_qp_g0w0 (gamma/2 is the half-line cosine transform).  Any output may be
+ * NULL to skip it.  fit_err[3] (may be NULL): for gamma, delta, s_weights the
+ * largest deviation over 997 energies divided by the largest target value
+ * (0 for a skipped output).  Host code only: needs no context and no GPU;
+ * thread-safe.  Errors: GW_ERR_INVALID_ARG (null grid, n_tau or n_omega
+ * outside 1..400, a grid point <= 0, e_max <= e_min or e_min <= 0),
+ * GW_ERR_NONFINITE. */
+int gw_transform_weights(const double* tau, int n_tau, const double* omega, int n_omega,
+                         double e_min, double e_max, double* gamma, double* delta,
+                         double* s_weights, double* fit_err);
 
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);

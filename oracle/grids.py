@@ -239,3 +239,35 @@ def minimax_grid(kind: str, n: int, e_min: float, e_max: float):
     if kind == "T":
         return p / e_min, a / e_min, e / e_min
     return p * e_min, a * e_min, e / e_min
+
+
+def _fit_x(e_min: float, e_max: float, m: int) -> np.ndarray:
+    return e_min * (e_max / e_min) ** (np.arange(m) / (m - 1))
+
+
+def transform_weights(tau, omega, e_min: float, e_max: float):
+    """Least-squares transform weights for decaying exponentials exp(-x|tau|),
+    x on 400 log-spaced energies of [e_min, e_max] (minimum-norm, singular
+    values below 1e-14 of the largest dropped):
+      gamma [n_omega, n_tau]: sum_j gamma_kj exp(-x tau_j) ~ 2x/(x^2 + omega_k^2)
+      delta [n_tau, n_omega]: sum_k delta_jk 2x/(x^2 + omega_k^2) ~ exp(-x tau_j)
+      s     [n_omega, n_tau]: sum_j s_kj exp(-x tau_j) ~ omega_k/(x^2 + omega_k^2)
+    and the three fit errors (max deviation over 997 energies / max target)."""
+    tau = np.asarray(tau, float)
+    omega = np.asarray(omega, float)
+
+    def parts(x):
+        e = np.exp(-np.outer(x, tau))
+        c = 2.0 * x[:, None] / (x[:, None] ** 2 + omega[None, :] ** 2)
+        s = omega[None, :] / (x[:, None] ** 2 + omega[None, :] ** 2)
+        return e, c, s
+
+    e, c, s = parts(_fit_x(e_min, e_max, 400))
+    gamma = np.linalg.lstsq(e, c, rcond=1e-14)[0].T
+    delta = np.linalg.lstsq(c, e, rcond=1e-14)[0].T
+    sw = np.linalg.lstsq(e, s, rcond=1e-14)[0].T
+    e, c, s = parts(_fit_x(e_min, e_max, 997))
+    err = np.array([np.abs(e @ gamma.T - c).max() / np.abs(c).max(),
+                    np.abs(c @ delta.T - e).max() / np.abs(e).max(),
+                    np.abs(e @ sw.T - s).max() / np.abs(s).max()])
+    return gamma, delta, sw, err

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("gw_mlp_train", _I, [_P, _P, _P, _LL, _I, _LL, ctypes.c_float, ctypes.c_ulonglong, _P]),
     ("gw_mlp_predict", _I, [_P, _P, _LL, _P]),
     ("gw_minimax_grid", _I, [_I, _I, _D, _D, _P, _P, ctypes.POINTER(_D)]),
+    ("gw_transform_weights", _I, [_P, _I, _P, _I, _D, _D, _P, _P, _P, _P]),
 ]
 
 MLP_FEATURES = 8
@@ -158,6 +159,24 @@ def gw_minimax_grid(kind: int, n: int, e_min: float, e_max: float):
     if rc != GW_OK:
         raise GwError(rc, "gw_minimax_grid")
     return nodes[:n], weights[:n], err.value
+
+
+def gw_transform_weights(tau, omega, e_min: float, e_max: float):
+    """(gamma [n_omega, n_tau], delta [n_tau, n_omega], s [n_omega, n_tau],
+    fit errors [3]) for the grids tau and omega and transition energies in
+    [e_min, e_max].  Host code: needs no context and no GPU."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    nt, nw = len(tau), len(omega)
+    gamma = np.zeros((max(nw, 1), max(nt, 1)))
+    delta = np.zeros((max(nt, 1), max(nw, 1)))
+    s = np.zeros((max(nw, 1), max(nt, 1)))
+    err = np.zeros(3)
+    rc = lib().gw_transform_weights(_ptr(tau), nt, _ptr(omega), nw, float(e_min), float(e_max),
+                                    _ptr(gamma), _ptr(delta), _ptr(s), _ptr(err))
+    if rc != GW_OK:
+        raise GwError(rc, "gw_transform_weights")
+    return gamma, delta, s, err
 
 
 def gw_create(device: int = 0, stream: int | None = None) -> int:

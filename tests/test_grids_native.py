@@ -114,3 +114,48 @@ def test_minimax_grids_fit_the_transforms_better_than_log_grids(lib, n):
     (lg, ls), (mg, ms) = errs
     print(f"n={n}: cosine fit {lg:.2e} (log) {mg:.2e} (minimax); sine {ls:.2e} {ms:.2e}")
     assert mg < 0.5 * lg and ms < 0.5 * ls
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_transform_weights_match_oracle(lib, n):
+    """Library weights (one-sided Jacobi SVD) against the oracle's (numpy
+    lstsq) on the log grid and on minimax grids of the synthetic spectrum;
+    well-conditioned sizes agree elementwise, and the fit errors agree."""
+    gap, width = 0.3, 2.3
+    tl = 0.01 * 5000.0 ** (np.arange(n) / (n - 1))
+    ol = 0.15 * (9.2 / 0.15) ** (np.arange(n) / (n - 1))
+    tm = lib.gw_minimax_grid(lib.GW_GRID_TIME, n, gap, width)[0]
+    om = lib.gw_minimax_grid(lib.GW_GRID_FREQ, n, gap, width)[0]
+    for tau, omega in ((tl, ol), (tm, om)):
+        got = lib.gw_transform_weights(tau, omega, gap, width)
+        ref = og.transform_weights(tau, omega, gap, width)
+        for g, r in zip(got[:3], ref[:3]):
+            assert np.abs(g - r).max() <= 1e-8 * np.abs(r).max()
+        np.testing.assert_allclose(got[3], ref[3], rtol=1e-6)
+
+
+def test_transform_weights_ill_conditioned_fit_as_well(lib):
+    """Twenty log-spaced points for R = 7.7: the columns are dependent to
+    1e-14, the truncated solutions differ, but they fit equally well."""
+    n, gap, width = 20, 0.3, 2.3
+    tau = 0.01 * 5000.0 ** (np.arange(n) / (n - 1))
+    omega = 0.15 * (9.2 / 0.15) ** (np.arange(n) / (n - 1))
+    got = lib.gw_transform_weights(tau, omega, gap, width)
+    ref = og.transform_weights(tau, omega, gap, width)
+    assert np.all(got[3] <= 1.05 * ref[3]) and np.all(got[3] < 1e-7)
+
+
+def test_transform_weights_arguments(lib):
+    f = lib.lib().gw_transform_weights
+    t = np.array([0.5, 1.0])
+    w = np.array([0.5, 1.0])
+    out = np.zeros(4)
+    p = out.ctypes.data
+    assert f(None, 2, w.ctypes.data, 2, 0.3, 2.3, p, p, p, None) == -1
+    assert f(t.ctypes.data, 0, w.ctypes.data, 2, 0.3, 2.3, p, p, p, None) == -1
+    assert f(t.ctypes.data, 2, w.ctypes.data, 2, 2.3, 0.3, p, p, p, None) == -1
+    bad = np.array([0.5, -1.0])
+    assert f(bad.ctypes.data, 2, w.ctypes.data, 2, 0.3, 2.3, p, p, p, None) == -1
+    nan = np.array([0.5, np.nan])
+    assert f(t.ctypes.data, 2, nan.ctypes.data, 2, 0.3, 2.3, p, p, p, None) == -4
+    assert f(t.ctypes.data, 2, w.ctypes.data, 2, 0.3, 2.3, None, None, None, None) == 0

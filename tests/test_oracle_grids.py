@@ -132,3 +132,44 @@ def test_physical_grid_bounds_the_energy_denominator(kind):
     dev = np.abs(1.0 / E - approx)
     assert dev.max() <= err * (1 + 1e-6)
     assert dev.max() >= err * (1 - 1e-4)
+
+
+def test_transform_weights_solve_the_normal_equations():
+    """Well-conditioned case (4 points): the weights equal the solution of the
+    normal equations A^T A w = A^T f, a second route, and the residual is
+    orthogonal to every column."""
+    tau = np.array([0.2, 0.9, 3.0, 9.0])
+    omega = np.array([0.2, 0.7, 2.0, 5.0])
+    gamma, delta, sw, err = og.transform_weights(tau, omega, 0.3, 2.3)
+    x = 0.3 * (2.3 / 0.3) ** (np.arange(400) / 399)
+    e = np.exp(-np.outer(x, tau))
+    c = 2.0 * x[:, None] / (x[:, None] ** 2 + omega ** 2)
+    s = omega / (x[:, None] ** 2 + omega ** 2)
+    for a, f, w in ((e, c, gamma), (c, e, delta), (e, s, sw)):
+        ref = np.linalg.solve(a.T @ a, a.T @ f).T
+        np.testing.assert_allclose(w, ref, rtol=1e-6, atol=1e-9 * np.abs(ref).max())
+        r = a @ w.T - f
+        assert np.abs(a.T @ r).max() <= 1e-9 * np.abs(a).max() * np.abs(f).max() * len(x)
+    assert np.all(err > 0) and np.all(err < 0.1)
+
+
+def test_transform_weights_reproduce_the_closed_form_transform():
+    """chi(tau) = exp(-x|tau|) for an energy x inside the range: the cosine
+    weights give its full-line transform 2x/(x^2 + omega^2), the sine weights
+    omega/(x^2 + omega^2), within the reported fit errors; errors fall as
+    points are added."""
+    errs = []
+    for n in (6, 8, 10):
+        tau = 0.01 * 5000.0 ** (np.arange(n) / (n - 1))
+        omega = 0.15 * (9.2 / 0.15) ** (np.arange(n) / (n - 1))
+        gamma, _, sw, err = og.transform_weights(tau, omega, 0.3, 2.3)
+        xs = 0.3 * (2.3 / 0.3) ** (np.arange(997) / 996)
+        top_c = np.max(2 * xs[:, None] / (xs[:, None] ** 2 + omega ** 2))
+        top_s = np.max(omega / (xs[:, None] ** 2 + omega ** 2))
+        for x in (0.31, 0.77, 2.29):
+            cos_ft = 2 * x / (x * x + omega ** 2)
+            sin_ft = omega / (x * x + omega ** 2)
+            assert np.abs(gamma @ np.exp(-x * tau) - cos_ft).max() <= 1.01 * err[0] * top_c
+            assert np.abs(sw @ np.exp(-x * tau) - sin_ft).max() <= 1.01 * err[2] * top_s
+        errs.append(err)
+    assert errs[0][0] > errs[1][0] > errs[2][0]

@@ -373,6 +373,7 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
                   double thr, double* acc, std::vector<double>& fc_host, int /*precision*/,
                   size_t batch_idx) {
   const int ns = b.s1 - b.s0;
+  gw::TraceRange trace("chi: batch, CUDA cores");
   const int prow = b.P1 - b.P0;
   const long long Kb = b.Kb;
   int rc;
@@ -678,6 +679,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
                      double thr, double* acc, std::vector<double>& fc_host, int precision,
                      size_t batch_idx) {
   const int slices = precision == GW_BF16X6 ? 3 : 2;
+  gw::TraceRange trace("chi: batch, tensor cores");
   const int f16 = precision == GW_FP16X3;
   const double prods = slices == 3 ? 6.0 : 3.0;
   const int tile = gw::tc_tile_rows();
@@ -1449,6 +1451,7 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out) {
 int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precision, int screening,
                double* chi_out, int out_on_device) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_chi_tau");
   ctx->err.clear();
   if (ctx->n_at == 0 || ctx->d_t3 == nullptr && ctx->n_blocks > 0)
     return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_basis and gw_set_3c_tensor first");
@@ -1519,10 +1522,11 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   for (long long b = 0; b < ctx->n_blocks; ++b)
     if (!(ctx->blk_norm[b] < thr)) kept_blocks.push_back((int)b);
 
-  cudaEvent_t ev[8];
-  for (auto& e : ev) GW_TRY(cudaEventCreate(&e));
+  gw::ScopedEvents<3> ev;
+  GW_TRY(ev.create());
   double ms_g = 0, ms_c = 0;
   for (int j = tau_first; j < tau_first + tau_count; ++j) {
+    gw::TraceRange trace_tau("chi: one tau point");
     GW_TRY(cudaEventRecord(ev[0], ctx->stream));
     ctx->cur_tau = ctx->tau[j];
     gw::launch_greens(ctx->d_C, ctx->d_eps, nao, ctx->n_occ, ctx->mu, ctx->tau[j], cso, csv, go, gv,
@@ -1614,7 +1618,6 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     ctx->stats.flops_b += fb;
     ctx->stats.flops_c += fcs;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   ctx->stats.flops_useful = ctx->stats.flops_a + ctx->stats.flops_b + ctx->stats.flops_c;
   ctx->stats.tasks_seen = ctx->mlp_seen;
   ctx->stats.tasks_skipped = ctx->mlp_skipped;

@@ -33,6 +33,7 @@ extern "C" int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const doub
                            const double* delta, const double* chi_tau, int chi_on_device,
                            double* w_tau_out, int out_on_device) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_chi_to_w");
   ctx->err.clear();
   if (ctx->n_at == 0 || !ctx->have_greens) {
     ctx->err = "gw_chi_to_w: call gw_set_basis and gw_set_greens first (the tau grid)";
@@ -140,6 +141,7 @@ extern "C" int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const doub
 extern "C" int gw_ri_metric(gw_ctx* ctx, const double* S, int n_mat, const double* M, int m_on_device,
                             double* out, int out_on_device) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_ri_metric");
   ctx->err.clear();
   if (ctx->n_at == 0) {
     ctx->err = "gw_ri_metric: call gw_set_basis first (the RI size)";

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <map>
@@ -12,6 +13,33 @@
 #include "../../include/gwchi.h"
 
 namespace gw {
+
+// Named NVTX range over a scope, for profilers (Nsight Compute's --nvtx
+// filters, timeline tools); costs a predicted branch when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// CUDA events destroyed with the scope, also on early error returns.
+template <int N>
+struct ScopedEvents {
+  cudaEvent_t ev[N];
+  int made = 0;
+  cudaError_t create() {
+    for (; made < N; ++made) {
+      const cudaError_t e = cudaEventCreate(&ev[made]);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaEvent_t operator[](int i) const { return ev[i]; }
+  ~ScopedEvents() {
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  }
+};
 
 // Slab: 64 consecutive primary functions mu of one sigma-atom segment of the
 // K dimension of the step-C operands.

@@ -113,6 +113,7 @@ extern "C" int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const 
                           const double* eps, const double* vxc, const double* sx, double* qp_out,
                           int* iters_out) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_qp_g0w0");
   ctx->err.clear();
   if (n_orb <= 0 || n_tau <= 0 || n_omega <= 1 || n_omega > kMaxOmega || !sigma_c || !omega ||
       !gamma || !s_weights || !eps || !vxc || !sx || !qp_out) {

@@ -329,6 +329,7 @@ int sigma_impl(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orb
 extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orbitals,
                             int n_orb, double thr, int precision, double* sigma_out) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_sigma_tau");
   ctx->err.clear();
   if (!ctx->have_greens) {
     ctx->err = "gw_sigma_tau: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
@@ -343,6 +344,7 @@ extern "C" int gw_sigma_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, c
 extern "C" int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const int* orbitals,
                           int n_orb, double thr, int precision, double* sx_out) {
   if (!ctx) return GW_ERR_INVALID_ARG;
+  gw::TraceRange trace("gw_sigma_x");
   ctx->err.clear();
   if (!ctx->have_greens) {
     ctx->err = "gw_sigma_x: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";

@@ -123,7 +123,10 @@ double sumsq(const std::vector<double>& v) {
 }
 
 // Levenberg-Marquardt with Marquardt's column scaling: each step solves
-// [J; sqrt(mu) D] dz = [-F; 0] in the least-squares sense.
+// [J; sqrt(mu) D] dz = [-F; 0] in the least-squares sense.  The damping starts
+// near Gauss-Newton (the levelled system is square and usually well started)
+// and follows Nielsen's rule: scaled by max(1/3, 1 - (2 rho - 1)^3) after an
+// accepted step with gain ratio rho, by 2, 4, 8, ... after rejected ones.
 void level(int kind, const std::vector<double>& X, Approx& f, double& lam, double& budget) {
   const int n = static_cast<int>(f.a.size());
   const int N = 2 * n + 1;
@@ -134,7 +137,7 @@ void level(int kind, const std::vector<double>& X, Approx& f, double& lam, doubl
   }
   z[2 * n] = lam;
   if (!level_residual(kind, X, z, F)) return;
-  double mu = 1e-3, fs = sumsq(F);
+  double mu = 1e-12, fs = sumsq(F), nu = 2.0;
   std::vector<double> A(static_cast<size_t>(2 * N) * N), b(2 * N);
   for (int it = 0; it < 2000 && fs > 0.0 && budget > 0; ++it) {
     // Jacobian rows at z
@@ -174,16 +177,27 @@ void level(int kind, const std::vector<double>& X, Approx& f, double& lam, doubl
       }
       if (level_residual(kind, X, zn, Fn) && sumsq(Fn) < fs) {
         const double fs_old = fs;
+        // gain ratio against the linear model ||F + J dz||^2
+        double model = 0.0;
+        for (int i = 0; i < N; ++i) {
+          double r = F[i];
+          for (int c = 0; c < N; ++c) r += A[i * N + c] * dz[c];
+          model += r * r;
+        }
+        const double rho = (fs_old - sumsq(Fn)) / std::max(fs_old - model, 1e-300);
         z.swap(zn);
         F.swap(Fn);
         fs = sumsq(F);
-        mu = std::max(mu * 0.3, 1e-20);
+        const double t = 2.0 * rho - 1.0;
+        mu = std::max(mu * std::max(1.0 / 3.0, 1.0 - t * t * t), 1e-20);
+        nu = 2.0;
         accepted = true;
         // converged: the residual no longer falls, or sits at rounding level
         if (fs_old - fs <= 1e-12 * fs_old || fs <= 1e-30 * N) step = 0.0;
         break;
       }
-      mu *= 10.0;
+      mu *= nu;
+      nu *= 2.0;
       if (step < 1e-16) break;
     }
     if (!accepted || step < 1e-15) break;

@@ -333,6 +333,29 @@ int gw_transform_weights(const double* tau, int n_tau, const double* omega, int 
                          double e_min, double e_max, double* gamma, double* delta,
                          double* s_weights, double* fit_err);
 
+/* Eigenvalue-self-consistent GW (the paragraph after Eq. 12).  Each cycle
+ * builds G of Eq. 2 from the current levels and runs gw_chi_tau (all tau
+ * points, filter thr, `precision`, bound screening), gw_chi_to_w (V, gamma,
+ * delta), gw_sigma_tau for `orbitals` and gw_qp_g0w0 (omega, gamma,
+ * s_weights, vxc, and Sigma^x_n of gw_sigma_x computed once).  The
+ * quasiparticle equation keeps the levels given to gw_set_greens as eps_n.
+ * The next cycle's levels: each level moves by the shift e_k - eps_k of the
+ * nearest listed orbital on its side of the gap (nearest by index; on a tie
+ * the one nearer the gap; a side with no listed orbital keeps its levels);
+ * with HOMO and LUMO listed this is the scissor shift.  The first cycle is
+ * G0W0.  Stops when no energy changes by tol or more between two cycles.
+ * Arrays as in the calls above, host memory; qp_out[n_orb] receives the last
+ * energies and cycles_out (may be NULL) the cycles run.  The context's levels
+ * are restored before return.  Errors: those of the calls above;
+ * GW_ERR_ORDER (inputs missing); GW_ERR_INVALID_ARG (null array, n_orb < 1,
+ * orbital out of range, n_omega < 2, max_cycles < 1, tol <= 0);
+ * GW_ERR_NOT_CONVERGED after max_cycles, or when a shifted level crosses
+ * mu_fermi (qp_out then holds the last energies). */
+int gw_evgw(gw_ctx* ctx, const double* V, int n_omega, const double* omega, const double* gamma,
+            const double* delta, const double* s_weights, const int* orbitals, int n_orb,
+            const double* vxc, double thr, int precision, int max_cycles, double tol,
+            double* qp_out, int* cycles_out);
+
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
 

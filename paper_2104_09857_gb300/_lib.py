@@ -104,6 +104,8 @@ SIGNATURES = [
     ("gw_mlp_predict", _I, [_P, _P, _LL, _P]),
     ("gw_minimax_grid", _I, [_I, _I, _D, _D, _P, _P, ctypes.POINTER(_D)]),
     ("gw_transform_weights", _I, [_P, _I, _P, _I, _D, _D, _P, _P, _P, _P]),
+    ("gw_evgw", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I, _D, _P,
+                     ctypes.POINTER(_I)]),
 ]
 
 MLP_FEATURES = 8
@@ -146,6 +148,25 @@ def _check(ctx, rc: int) -> None:
 # ---------------------------------------------------------------------------
 # thin functions with the C names
 # ---------------------------------------------------------------------------
+
+def gw_evgw(ctx: int, v, omega, gamma, delta, s_weights, orbitals, vxc, thr: float,
+            precision: int = GW_FP64, max_cycles: int = 20, tol: float = 1e-6):
+    """(energies [n_orb], cycles run) of eigenvalue-self-consistent GW for the
+    listed orbitals; all inputs host arrays."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    s_weights = np.ascontiguousarray(s_weights, dtype=np.float64)
+    orbitals = np.ascontiguousarray(orbitals, dtype=np.int32)
+    vxc = np.ascontiguousarray(vxc, dtype=np.float64)
+    out = np.zeros(len(orbitals))
+    cycles = _I(0)
+    _check(ctx, lib().gw_evgw(ctx, _ptr(v), len(omega), _ptr(omega), _ptr(gamma), _ptr(delta),
+                              _ptr(s_weights), _ptr(orbitals), len(orbitals), _ptr(vxc), thr,
+                              precision, max_cycles, tol, _ptr(out), ctypes.byref(cycles)))
+    return out, cycles.value
+
 
 def gw_minimax_grid(kind: int, n: int, e_min: float, e_max: float):
     """(nodes [n], weights [n], max_err) of the minimax time (GW_GRID_TIME) or

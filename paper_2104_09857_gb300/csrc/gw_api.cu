@@ -153,6 +153,7 @@ void reset_greens(gw_ctx* ctx) {
   ctx->d_C = ctx->d_eps = nullptr;
   ctx->have_greens = false;
   ctx->tau.clear();
+  ctx->h_eps.clear();
 }
 
 struct Timer {
@@ -1366,6 +1367,7 @@ int gw_set_greens(gw_ctx* ctx, const double* C, const double* eps, int n_occ, do
   ctx->n_occ = n_occ;
   ctx->mu = mu_fermi;
   ctx->tau.assign(tau, tau + n_tau);
+  ctx->h_eps.assign(eps, eps + nao);
   ctx->have_greens = true;
   return GW_OK;
 }

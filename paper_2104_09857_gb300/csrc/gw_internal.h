@@ -148,6 +148,7 @@ struct gw_ctx {
   bool have_greens = false;
   double* d_C = nullptr;
   double* d_eps = nullptr;
+  std::vector<double> h_eps;  // host copy of the levels given to gw_set_greens
   int n_occ = 0;
   double mu = 0.0;
   std::vector<double> tau;

@@ -4,8 +4,9 @@ chain, Sigma^x, Sigma^c, the quasiparticle step) cycle after cycle, so it is
 the last file of the suite.
 
 Inputs as in tests/test_oracle_evgw.py: benzene, 10 tau points, V scaled by
-3e-4, vxc = Sigma^x.  The Pade step amplifies rounding about 1e5-fold, so the
-energies are compared at 1e-7 Ha."""
+3e-4, vxc = Sigma^x.  The Pade step amplifies rounding about 1e5-fold and
+each cycle feeds the last one's energies back, so the energies are compared
+at 1e-6 Ha (0.03 meV)."""
 
 import numpy as np
 import pytest
@@ -56,7 +57,7 @@ def test_evgw_matches_oracle_and_restores_levels(pkg):
         chi = ctx.chi_tau(case.thr, "fp64", 0, 1).cpu().numpy()
     print(f"evGW HOMO/LUMO {got} after {cycles} cycles; oracle {ref} after {ref_cycles}")
     assert abs(cycles - ref_cycles) <= 1
-    assert np.max(np.abs(got - ref)) < 1e-7
+    assert np.max(np.abs(got - ref)) < 1e-6
     # the context is back on the levels given to gw_set_greens
     chi_ref = oc.chi_dense(case, tau_index=0)[0]
     assert np.linalg.norm(chi[0] - chi_ref) <= 1e-10 * np.linalg.norm(chi_ref)

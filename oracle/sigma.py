@@ -113,3 +113,28 @@ def sigma_blocks(case, w_tau: np.ndarray, orbitals, tau_indices, thr: float | No
             out[a, jj, 0] = -s_term(go, b, w_tau[j])
             out[a, jj, 1] = s_term(gv, b, w_tau[j])
     return out
+
+
+def sigma_ao_dense(case, w_tau: np.ndarray, thr: float | None = None) -> np.ndarray:
+    """The full atomic-orbital matrix of Eq. 10 (the form before it is
+    projected on orbital n): [n_tau][2][n_AO][n_AO] with
+        [j][0] = Sigma^c_{mu nu}(i tau_j)  = -sum_{lam sig P Q} (mu lam|P) G^occ_{lam sig} W_PQ (sig nu|Q)
+        [j][1] = Sigma^c_{mu nu}(-i tau_j) = +sum ... G^virt ...
+    (the real representation of the diagonal oracle: C_n^T Sigma C_n is
+    Sigma^c_n).  The filter acts on the inputs: 3c blocks and G blocks with
+    Frobenius norm < thr are dropped."""
+    sysm = case.system
+    thr = case.thr if thr is None else thr
+    ao = oc.offsets(sysm.n_ao)
+    t = oc.dense_three_center(sysm.n_ao, sysm.n_ri, case.t3c.blocks, case.t3c.offsets,
+                              case.t3c.data, thr)
+    nao = t.shape[0]
+    out = np.zeros((len(case.tau), 2, nao, nao))
+    for j, tau in enumerate(case.tau):
+        go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, tau)
+        go = oc.filter_sym_2d(go, ao, thr)
+        gv = oc.filter_sym_2d(gv, ao, thr)
+        tw = np.einsum("snq,pq->snp", t, w_tau[j])          # (sig nu|Q) W_PQ summed over Q
+        for k, (g, sign) in enumerate(((go, -1.0), (gv, 1.0))):
+            out[j, k] = sign * np.einsum("mlp,ls,snp->mn", t, g, tw, optimize=True)
+    return out

@@ -77,3 +77,62 @@ def test_molecule_set_shapes():
         assert 8 <= m.n_atoms <= 160
         nc = m.species.count("C")
         assert abs(nc - 2 * (m.n_atoms - nc)) <= 4  # about 2:1
+
+
+def _sigma_ao_case():
+    from synth.chain_inputs import synthetic_w
+
+    case = make_case("chain_CHCH")
+    w = synthetic_w(case.system.nri_total, case.tau, 4)
+    return case, w
+
+
+def test_sigma_ao_projects_onto_the_diagonal_self_energy():
+    """C_n^T Sigma_AO C_n is Sigma^c_n of the half-transformed route."""
+    case, w = _sigma_ao_case()
+    full = osg.sigma_ao_dense(case, w, thr=0.0)
+    orbs = list(range(case.system.nao_total))
+    diag = osg.sigma_dense(case, w, orbs, thr=0.0)
+    proj = np.einsum("mn,jkmv,vn->njk", case.C, full, case.C)
+    np.testing.assert_allclose(proj, diag, rtol=1e-11, atol=1e-13 * np.abs(diag).max())
+
+
+def test_sigma_ao_symmetry_and_signs():
+    """Symmetric; with W negative semidefinite, Sigma(i tau) is positive
+    semidefinite (G^occ >= 0 between T^P-weighted factors) and Sigma(-i tau)
+    negative semidefinite."""
+    case, w = _sigma_ao_case()
+    full = osg.sigma_ao_dense(case, w, thr=0.0)
+    for j in range(len(case.tau)):
+        for k, sign in ((0, 1.0), (1, -1.0)):
+            m = full[j, k]
+            np.testing.assert_allclose(m, m.T, rtol=0, atol=1e-13 * np.abs(m).max())
+            ev = np.linalg.eigvalsh(0.5 * (m + m.T))
+            assert np.all(sign * ev >= -1e-12 * np.abs(ev).max())
+
+
+def test_sigma_ao_brute_force_on_two_atoms():
+    """Explicit loops over mu, nu, lambda, sigma, P, Q on the two-atom chain."""
+    from synth.chain_inputs import synthetic_w
+
+    case = make_case("chain_HH")
+    sysm = case.system
+    w = synthetic_w(sysm.nri_total, case.tau, 5)
+    full = osg.sigma_ao_dense(case, w, thr=0.0)
+    t = oc.dense_three_center(sysm.n_ao, sysm.n_ri, case.t3c.blocks, case.t3c.offsets,
+                              case.t3c.data, 0.0)
+    nao, nri = t.shape[0], t.shape[2]
+    j = 1
+    go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, case.tau[j])
+    for g, k, sign in ((go, 0, -1.0), (gv, 1, 1.0)):
+        ref = np.zeros((nao, nao))
+        for mu in range(nao):
+            for nu in range(nao):
+                acc = 0.0
+                for lam in range(nao):
+                    for sig in range(nao):
+                        for p in range(nri):
+                            for q in range(nri):
+                                acc += t[mu, lam, p] * g[lam, sig] * w[j, p, q] * t[sig, nu, q]
+                ref[mu, nu] = sign * acc
+        np.testing.assert_allclose(full[j, k], ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())

@@ -41,7 +41,7 @@ enum gw_status {
   GW_ERR_CUDA = -6,        /* a CUDA runtime call or kernel failed           */
   GW_ERR_TIMEOUT = -7,     /* a bounded device wait gave up                  */
   GW_ERR_NOT_SPD = -8,     /* a Cholesky factorisation met a non-positive pivot */
-  GW_ERR_UNSUPPORTED = -9, /* option not available in this build             */
+  GW_ERR_UNSUPPORTED = -9, /* combination of options the library does not offer */
   GW_ERR_NOT_CONVERGED = -10 /* an iterative host solve did not converge       */
 };
 
@@ -208,8 +208,8 @@ int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const double* gamma,
  * drained.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double* chi_out_device);
 
-/* Learned screening of step-C tasks.  Not in the paper: an addition of the
- * hot-path specification.  A task is one (128 x 128 chi tile, 64-function K
+/* Learned screening of step-C tasks.  Not in the paper: a learned predictor
+ * of block norms that skips work on top of the exact filter.  A task is one (128 x 128 chi tile, 64-function K
  * slab) pair of the tensor-core route that survives the exact block filter;
  * its 8 features are log10 of the norm bounds of its X and Y parts (from the
  * accumulated atom-block norms), log10 tau, three centroid distances (sigma

@@ -1,5 +1,5 @@
-"""Oracle for the learned block-norm predictor (not in the paper: an addition
-of the hot-path specification).  FP64 numpy forward and backward of a
+"""Oracle for the learned block-norm predictor (not in the paper: a learned
+skip of tasks on top of the exact block filter).  FP64 numpy forward and backward of a
 2-hidden-layer ReLU network whose weights are rounded to bfloat16 before use
 (the GPU keeps FP32 master weights and multiplies with their bf16 copies,
 accumulating in FP32), with a mean-squared-error loss on log10 norms.

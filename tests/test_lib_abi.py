@@ -54,3 +54,49 @@ def test_create_without_device_fails_cleanly(built):
 
     with pytest.raises(_lib.GwError):
         _lib.gw_create(0, None)
+
+
+C_PROGRAM = r"""
+#include <math.h>
+#include <stdio.h>
+#include "gwchi.h"
+
+int main(void) {
+  double tau[6], a[6], omega[6], b[6], err_t, err_w, gamma[36], delta[36], s[36], fit[3];
+  if (gw_minimax_grid(GW_GRID_TIME, 6, 0.3, 2.3, tau, a, &err_t) != GW_OK) return 1;
+  if (gw_minimax_grid(GW_GRID_FREQ, 6, 0.3, 2.3, omega, b, &err_w) != GW_OK) return 2;
+  if (gw_transform_weights(tau, 6, omega, 6, 0.3, 2.3, gamma, delta, s, fit) != GW_OK) return 3;
+  if (gw_minimax_grid(GW_GRID_TIME, 0, 0.3, 2.3, tau, a, &err_t) != GW_ERR_INVALID_ARG) return 4;
+  /* 1/E from the time grid at E = 1 */
+  double sum = 0.0;
+  for (int j = 0; j < 6; ++j) sum += a[j] * exp(-tau[j]);
+  printf("%.17g %.17g %.17g %.17g\n", err_t, err_w, fit[0], fabs(sum - 1.0));
+  return fabs(sum - 1.0) <= err_t * 1.000001 ? 0 : 5;
+}
+"""
+
+
+def test_header_compiles_as_c_and_host_calls_link(built):
+    """A C99 program includes gwchi.h, links libgwchi and calls the host-code
+    entry points (grids and transform weights) without a GPU."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    work = os.path.join(ROOT, "paper_2104_09857_gb300", "_build")
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, "abi_check.c")
+    exe = os.path.join(work, "abi_check")
+    with open(src, "w") as f:
+        f.write(C_PROGRAM)
+    libdir = os.path.dirname(built)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        src, "-o", exe, "-L", libdir, "-lgwchi", "-lm", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    err_t, err_w, fit0, dev = (float(v) for v in r.stdout.split())
+    assert 0 < err_t < 1e-5 and 0 < err_w < 1e-5 and 0 < fit0 < 1e-2 and dev <= err_t * 1.000001

@@ -254,6 +254,21 @@ int gw_mlp_predict(gw_ctx* ctx, const float* feat, long long n, float* pred);
 int gw_ri_metric(gw_ctx* ctx, const double* S, int n_mat, const double* M, int m_on_device,
                  double* out, int out_on_device);
 
+/* The full atomic-orbital matrix of the correlation self-energy of Eq. 10,
+ * before projection on an orbital (C_n^T Sigma C_n is the Sigma^c_n of
+ * gw_sigma_tau):
+ *   Sigma_{mu nu}(+i tau) = -sum (mu lam|P) G^occ_{lam sig}(tau) W_PQ(tau) (sig nu|Q)
+ *   Sigma_{mu nu}(-i tau) = +sum (mu lam|P) G^virt_{lam sig}(tau) W_PQ(tau) (sig nu|Q)
+ * for every tau point of gw_set_greens.  FP64 dense route on the CUDA cores
+ * for molecules (n_AO^2 n_RI <= 3*2^30 and n_AO <= 2047, GW_ERR_INVALID_ARG
+ * otherwise; three arrays of n_AO^2 n_RI doubles on the device).  Filter: 3c
+ * blocks and G blocks with Frobenius norm < thr are dropped.  W_tau:
+ * [n_tau][n_ri][n_ri], device if w_on_device else host.  sigma_out:
+ * [n_tau][2][n_ao][n_ao] (index 0: +i tau, 1: -i tau), device if
+ * out_on_device else host. */
+int gw_sigma_ao_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, double thr,
+                    double* sigma_out, int out_on_device);
+
 /* Static exchange self-energy of Eq. 11 for the orbitals listed, with the RI
  * metric S = 1:
  *   Sigma^x_n = - sum_{mu nu} D_{mu nu} sum_{PQ} B^n_{mu P} V_PQ B^n_{nu Q},

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("gw_mlp_predict", _I, [_P, _P, _LL, _P]),
     ("gw_minimax_grid", _I, [_I, _I, _D, _D, _P, _P, ctypes.POINTER(_D)]),
     ("gw_transform_weights", _I, [_P, _I, _P, _I, _D, _D, _P, _P, _P, _P]),
+    ("gw_sigma_ao_tau", _I, [_P, _P, _I, _D, _P, _I]),
     ("gw_evgw", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I, _D, _P,
                      ctypes.POINTER(_I)]),
 ]
@@ -148,6 +149,14 @@ def _check(ctx, rc: int) -> None:
 # ---------------------------------------------------------------------------
 # thin functions with the C names
 # ---------------------------------------------------------------------------
+
+def gw_sigma_ao_tau(ctx: int, w_tau, n_tau: int, nao: int, thr: float) -> np.ndarray:
+    """Sigma_{mu nu}(+-i tau) [n_tau, 2, n_ao, n_ao] (host) from a host W."""
+    w = np.ascontiguousarray(w_tau, dtype=np.float64)
+    out = np.zeros((n_tau, 2, nao, nao))
+    _check(ctx, lib().gw_sigma_ao_tau(ctx, _ptr(w), 0, thr, _ptr(out), 0))
+    return out
+
 
 def gw_evgw(ctx: int, v, omega, gamma, delta, s_weights, orbitals, vxc, thr: float,
             precision: int = GW_FP64, max_cycles: int = 20, tol: float = 1e-6):

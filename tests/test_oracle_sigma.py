@@ -136,3 +136,45 @@ def test_sigma_ao_brute_force_on_two_atoms():
                                 acc += t[mu, lam, p] * g[lam, sig] * w[j, p, q] * t[sig, nu, q]
                 ref[mu, nu] = sign * acc
         np.testing.assert_allclose(full[j, k], ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+
+
+def test_sigma_ao_filter_drops_blocks_like_explicit_loops():
+    """thr > 0 on the four-atom chain: explicit per-block masks of the 3c
+    tensor and of G (blocks with Frobenius norm < thr zeroed, mirrors
+    together) reproduce the filtered AO self-energy."""
+    case = make_case("chain_CHCH")
+    s = case.system
+    w = synthetic_w(s.nri_total, case.tau, 6)
+    t_full = oc.dense_three_center(s.n_ao, s.n_ri, case.t3c.blocks, case.t3c.offsets,
+                                   case.t3c.data, 0.0)
+    ao, ri = oc.offsets(s.n_ao), oc.offsets(s.n_ri)
+    n_at = len(s.n_ao)
+    j = 2
+    go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, case.tau[j])
+    norms = [np.linalg.norm(t_full[ao[a]:ao[a + 1], ao[b]:ao[b + 1], ri[p]:ri[p + 1]])
+             for a in range(n_at) for b in range(a, n_at) for p in range(n_at)]
+    gnorms = [np.linalg.norm(g[ao[a]:ao[a + 1], ao[b]:ao[b + 1]])
+              for g in (go, gv) for a in range(n_at) for b in range(a, n_at)]
+    thr = float(np.median([x for x in norms + gnorms if x > 0]))   # drops about half
+    t = t_full.copy()
+    for a in range(n_at):
+        for b in range(a, n_at):
+            for p in range(n_at):
+                blk = (slice(ao[a], ao[a + 1]), slice(ao[b], ao[b + 1]), slice(ri[p], ri[p + 1]))
+                if np.linalg.norm(t[blk]) < thr:
+                    t[blk] = 0.0
+                    t[blk[1], blk[0], blk[2]] = 0.0
+    ref = []
+    for g, sign in ((go, -1.0), (gv, 1.0)):
+        g = g.copy()
+        for a in range(n_at):
+            for b in range(a, n_at):
+                if np.linalg.norm(g[ao[a]:ao[a + 1], ao[b]:ao[b + 1]]) < thr:
+                    g[ao[a]:ao[a + 1], ao[b]:ao[b + 1]] = 0.0
+                    g[ao[b]:ao[b + 1], ao[a]:ao[a + 1]] = 0.0
+        ref.append(sign * np.einsum("mlp,ls,pq,snq->mn", t, g, w[j], t, optimize=True))
+    got = osg.sigma_ao_dense(case, w, thr=thr)[j]
+    for k in range(2):
+        np.testing.assert_allclose(got[k], ref[k], rtol=1e-12, atol=1e-14 * np.abs(ref[k]).max())
+    full = osg.sigma_ao_dense(case, w, thr=0.0)[j]
+    assert np.abs(full - got).max() > 1e-6 * np.abs(full).max()      # the filter did act

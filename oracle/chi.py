@@ -278,25 +278,76 @@ class BlockOracle:
         sizes = self.n_ao[atoms]
         return offsets(sizes)
 
+    def _partners(self, atoms, tp):
+        """Per atom b of the slice: positions (in idx) of the functions of the
+        atoms a with a stored block (a, b, P) or (b, a, P) -- the only rows of
+        T[:, b, P] (and, T being symmetric in its primary indices, of
+        T[b, :, P]) that can be nonzero."""
+        sizes = self.n_ao[atoms]
+        cuts = offsets(sizes)
+        nz = np.abs(tp).sum(axis=2) > 0.0                        # [k, k]
+        nza = np.add.reduceat(np.add.reduceat(nz, cuts[:-1], axis=0), cuts[:-1], axis=1) > 0
+        out = []
+        for j in range(len(atoms)):
+            rows = [np.arange(cuts[i], cuts[i + 1]) for i in np.nonzero(nza[:, j])[0]]
+            out.append(np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64))
+        return cuts, out
+
     def m_slice(self, tau_index: int, p: int):
-        """M[mu, sigma in idx_p, P in p] = sum_lambda G^occ[mu, lambda] T[lambda, sigma, P], filtered."""
+        """M[mu, sigma in idx_p, P in p] = sum_lambda G^occ[mu, lambda] T[lambda, sigma, P], filtered.
+
+        Computed one sigma-atom b at a time: the lambda sum runs over the
+        functions of the atoms that share a stored block with b at this RI
+        atom (every other term is an exact zero of T), and each atom block
+        (mu-atom, b, p) of the result is dropped when its Frobenius norm is
+        < thr, the filter of chi_dense."""
         go, _ = self.greens(tau_index)
         idx, atoms, tp = self.t_slice(p)
         k = len(idx)
         npp = self.n_ri[p]
-        m = (go[:, idx] @ tp.reshape(k, k * npp)).reshape(-1, k, npp)
-        m = filter_3idx(m, [self.ao, self._atom_cuts(atoms), offsets([npp])], self.thr)
+        nao = go.shape[0]
+        cuts, part = self._partners(atoms, tp)
+        m = np.empty((nao, k, npp))
+        for j in range(len(atoms)):
+            lam = part[j]
+            c0, c1 = cuts[j], cuts[j + 1]
+            if lam.size == 0:
+                m[:, c0:c1, :] = 0.0
+                continue
+            tb = tp[lam, c0:c1, :].reshape(lam.size, (c1 - c0) * npp)
+            # G^occ is symmetric (Eq. 2): its columns idx[lam] are read as rows
+            r = go[idx[lam], :].T @ tb                            # [nao, nb * nP]
+            if self.thr > 0.0:
+                nrm = np.sqrt(np.add.reduceat(np.einsum("ij,ij->i", r, r), self.ao[:-1]))
+                r[np.repeat(nrm < self.thr, self.n_ao)] = 0.0
+            m[:, c0:c1, :] = r.reshape(nao, c1 - c0, npp)
         return idx, m
 
     def n_slice(self, tau_index: int, q: int):
-        """N[mu in idx_q, sigma, Q in q] = sum_nu T[mu, nu, Q] G^virt[nu, sigma], filtered."""
+        """N[mu in idx_q, sigma, Q in q] = sum_nu T[mu, nu, Q] G^virt[nu, sigma], filtered.
+
+        Computed one mu-atom a at a time: the nu sum runs over the functions of
+        the atoms that share a stored block with a at this RI atom, and each
+        atom block (a, sigma-atom, q) with Frobenius norm < thr is dropped."""
         _, gv = self.greens(tau_index)
         idx, atoms, tq = self.t_slice(q)
         k = len(idx)
         nq = self.n_ri[q]
-        # N[mu, sigma, Q] = sum_nu T[mu, nu, Q] G[nu, sigma]
-        n = np.einsum("mnq,ns->msq", tq, gv[idx, :], optimize=True)
-        n = filter_3idx(n, [self._atom_cuts(atoms), self.ao, offsets([nq])], self.thr)
+        nao = gv.shape[0]
+        cuts, part = self._partners(atoms, tq)
+        n = np.empty((k, nao, nq))
+        for i in range(len(atoms)):
+            nu = part[i]
+            c0, c1 = cuts[i], cuts[i + 1]
+            if nu.size == 0:
+                n[c0:c1] = 0.0
+                continue
+            ta = tq[c0:c1, nu, :].transpose(0, 2, 1).reshape((c1 - c0) * nq, nu.size)
+            r = ta @ gv[idx[nu], :]                               # [na * nQ, nao]
+            if self.thr > 0.0:
+                nrm = np.sqrt(np.add.reduceat(np.einsum("ij,ij->j", r, r), self.ao[:-1]))
+                r[:, np.repeat(nrm < self.thr, self.n_ao)] = 0.0
+            n[c0:c1] = r.reshape(c1 - c0, nq, nao).transpose(0, 2, 1)
         return idx, n
 
     def block(self, tau_index: int, p: int, q: int, cache: dict | None = None) -> np.ndarray:

@@ -201,11 +201,13 @@ int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const double* gamma,
  * GW_ERR_INVALID_ARG and a message giving the bytes needed.  The tensor
  * panels depend on thr and are built by gw_chi_tau: call it once with the same
  * thr first (GW_ERR_ORDER otherwise).  The first call on a device looks up
- * the array's device address and must come before any stream capture.  All
- * calls share the array: calls whose GPU work overlaps race and corrupt each
- * other's results.  chi_out_device: [n_ri_total][n_ri_total] FP64 on the
- * context's device.  Runs on the context's stream and returns after it has
- * drained.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture begins.  Each call copies its small per-batch
+ * tables from pageable host memory and synchronises the context's stream
+ * once per batch of sigma-atoms and once at its end.  All calls share the
+ * array: calls whose GPU work overlaps race and corrupt each other's results.
+ * chi_out_device: [n_ri_total][n_ri_total] FP64 on the context's device.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
 int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double* chi_out_device);
 
 /* Learned screening of step-C tasks.  Not in the paper: a learned predictor
@@ -220,7 +222,11 @@ int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double* chi_out_d
  * log10 of actual norm / bound) predicts log10 of the task's contribution
  * norm; with
  * screening = GW_SCREEN_MLP, gw_chi_tau drops a task when
- * prediction + margin < log10(thr) (option "mlp_margin", default 0.5).
+ * prediction + margin < log10(thr * min(1, B)) (option "mlp_margin", default
+ * 0.5), B the largest norm-product bound among the tasks of the task's chi
+ * tile: an absolute cut at thr where the tile's scale is 1 or more, a cut
+ * relative to the tile's scale where it is smaller (chi(i tau) falls as
+ * exp(-gap tau), and an absolute cut would dominate it at large tau).
  *
  * gw_mlp_log: run gw_chi_tau on the tensor-core route and record every task's
  *   features [n][8] and the log10 Frobenius norm of its actual contribution
@@ -293,9 +299,13 @@ int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const int* orbital
  *   e = eps[a] - vxc[a] + sx[a] + Re Sigma^c_n(e)
  * is solved by Newton-Raphson from eps[a] (derivative of Re Sigma^c by
  * central differences, step 1e-6; |step| < 1e-12 max(1, |e|); at most 100
- * iterations, count in iters_out[a] if not NULL).  sx is the exchange term
+ * iterations).  iters_out[a] (if not NULL) holds the iterations to
+ * convergence, or minus the iterations done when the solve of orbital a
+ * stopped without converging (a zero or non-finite derivative or step, or
+ * 100 iterations); then qp_out[a] is the last iterate and the call returns
+ * GW_ERR_NOT_CONVERGED after writing every output.  sx is the exchange term
  * of Eq. 11 and vxc the mean-field exchange-correlation level.  All arrays
- * are host memory; 2 <= n_omega <= 128, omega positive and distinct
+ * are host memory; 2 <= n_omega <= 128, every omega positive and all distinct
  * (GW_ERR_INVALID_ARG), finite inputs (GW_ERR_NONFINITE).  Independent of the
  * context's basis and tensor. */
 int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const double* sigma_c,

@@ -165,6 +165,12 @@ struct Timer {
 // ---------------------------------------------------------------------------
 int build_panels(gw_ctx* ctx, double thr) {
   if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
+  // the cached panels (and everything derived from them) stop being valid
+  // here: an allocation or copy below may fail and leave the pool half built
+  ctx->panels_ok = false;
+  ctx->panels_thr = -1.0;
+  ctx->pt_ok = false;
+  ctx->panel32_ok = false;
   ctx->ycov_valid = false;
   const int n = ctx->n_at;
   std::vector<int> kept;
@@ -664,13 +670,18 @@ int ensure_ycover(gw_ctx* ctx) {
       ok = false;
     }
   }
-  ctx->ycov_valid = true;
-  ctx->ycov_ok = ok;
-  if (!ok) return GW_OK;
+  if (!ok) {
+    ctx->ycov_ok = false;
+    ctx->ycov_valid = true;
+    return GW_OK;
+  }
+  // valid only once both tables are on the device
   GW_TRY(cudaMalloc(&ctx->d_ycov_lo, std::max(nri, 1) * sizeof(int)));
   GW_TRY(cudaMalloc(&ctx->d_ycov_hi, std::max(nri, 1) * sizeof(int)));
   GW_TRY(cudaMemcpy(ctx->d_ycov_lo, lo.data(), nri * sizeof(int), cudaMemcpyHostToDevice));
   GW_TRY(cudaMemcpy(ctx->d_ycov_hi, hi.data(), nri * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->ycov_ok = true;
+  ctx->ycov_valid = true;
   return GW_OK;
 }
 

@@ -161,8 +161,8 @@ int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb) {
   ML_TRY(cudaMemcpyAsync(kb.data(), mb.kacc, ntiles * sizeof(long long), cudaMemcpyDeviceToHost, st));
   gw::mlp_forward(ctx->d_mlp_wb, (float*)feat.p, slots, mb.counts, mb.nslab, nullptr, nullptr,
                   (float*)aux.p, st);
-  gw::mlp_compact(mb.tasks, mb.counts, mb.kacc, ntiles, mb.nslab, (float*)aux.p, (float)ctx->mlp_margin,
-                  (float)std::log10(mb.thr), mb.slab_len, (int*)skipped.p, st);
+  gw::mlp_compact(mb.tasks, mb.counts, mb.kacc, ntiles, mb.nslab, (float*)aux.p, (float*)feat.p,
+                  (float)ctx->mlp_margin, (float)std::log10(mb.thr), mb.slab_len, (int*)skipped.p, st);
   ML_TRY(cudaGetLastError());
   std::vector<int> h_sk(ntiles);
   ML_TRY(cudaMemcpyAsync(h_sk.data(), skipped.p, ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));

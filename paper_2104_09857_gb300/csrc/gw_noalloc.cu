@@ -28,6 +28,8 @@
 //  * The first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current) and caches it; make that
 //    first call before any stream capture begins.
+//  * Each call copies its per-batch tables from pageable host memory and
+//    synchronises the context's stream after every batch and at its end.
 //  * The 3c tensor panels are built by gw_chi_tau (they depend on thr); call
 //    gw_chi_tau once with the same thr before using this entry point.
 //  * No cudaMalloc, cudaFree or allocating library routine is called.

@@ -79,16 +79,30 @@ __global__ void k_qp(int n_orb, int n_tau, int n_om, const double* __restrict__ 
   }
   const double e0 = eps[a] - vxc[a] + sx[a];
   double e = eps[a];
-  int it = 1;
-  for (; it <= kMaxIter; ++it) {
+  // iterations to convergence, or -(iterations done) when the solve stopped
+  // without converging: a zero or non-finite derivative, a non-finite step,
+  // or kMaxIter steps
+  int status = -kMaxIter;
+  for (int it = 1; it <= kMaxIter; ++it) {
     const double f = e - (e0 + re_pade(e, u, omega, n_om));
     const double d = 1.0 - (re_pade(e + kH, u, omega, n_om) - re_pade(e - kH, u, omega, n_om)) / (2.0 * kH);
+    if (!(d != 0.0) || !isfinite(d) || !isfinite(f)) {
+      status = -it;
+      break;
+    }
     const double step = f / d;
+    if (!isfinite(step)) {
+      status = -it;
+      break;
+    }
     e -= step;
-    if (fabs(step) < kTol * fmax(1.0, fabs(e))) break;
+    if (fabs(step) < kTol * fmax(1.0, fabs(e))) {
+      status = it;
+      break;
+    }
   }
   out[a] = e;
-  iters[a] = it > kMaxIter ? kMaxIter : it;
+  iters[a] = status;
 }
 
 #define QP_TRY(call)                                                               \
@@ -120,12 +134,14 @@ extern "C" int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const 
     ctx->err = "gw_qp_g0w0: bad arguments (need n_orb, n_tau >= 1, 2 <= n_omega <= 128, non-null arrays)";
     return GW_ERR_INVALID_ARG;
   }
-  for (int k = 0; k < n_omega; ++k)
-    for (int l = 0; l < k; ++l)
-      if (!(omega[k] > 0.0) || omega[k] == omega[l]) {
-        ctx->err = "gw_qp_g0w0: frequencies must be positive and distinct";
-        return GW_ERR_INVALID_ARG;
-      }
+  for (int k = 0; k < n_omega; ++k) {
+    bool ok = omega[k] > 0.0;
+    for (int l = 0; l < k && ok; ++l) ok = omega[k] != omega[l];
+    if (!ok) {
+      ctx->err = "gw_qp_g0w0: frequencies must be positive and distinct";
+      return GW_ERR_INVALID_ARG;
+    }
+  }
   if (!all_finite(sigma_c, 2LL * n_orb * n_tau) || !all_finite(omega, n_omega) ||
       !all_finite(gamma, (long long)n_omega * n_tau) || !all_finite(s_weights, (long long)n_omega * n_tau) ||
       !all_finite(eps, n_orb) || !all_finite(vxc, n_orb) || !all_finite(sx, n_orb)) {
@@ -165,5 +181,12 @@ extern "C" int gw_qp_g0w0(gw_ctx* ctx, int n_orb, int n_tau, int n_omega, const 
   QP_TRY(cudaStreamSynchronize(st));
   if (iters_out)
     for (int a = 0; a < n_orb; ++a) iters_out[a] = it[a];
+  for (int a = 0; a < n_orb; ++a)
+    if (it[a] <= 0) {
+      ctx->err = "gw_qp_g0w0: the Newton solve of orbital " + std::to_string(a) +
+                 " did not converge (" + std::to_string(-it[a]) +
+                 " iterations; zero or non-finite derivative, or the iteration limit)";
+      return GW_ERR_NOT_CONVERGED;
+    }
   return GW_OK;
 }

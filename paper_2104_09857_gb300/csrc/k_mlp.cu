@@ -270,21 +270,29 @@ __global__ void k_round(const float* __restrict__ theta, __nv_bfloat16* __restri
 // per tile: keep task i iff pred + margin >= log_thr (order kept); rewrites
 // the list, its count and its K total; skipped[t] = tasks dropped
 __global__ void k_compact(int* __restrict__ tasks, int* __restrict__ counts, long long* __restrict__ kacc,
-                          int nslab, const float* __restrict__ pred, float margin, float log_thr,
-                          const int* __restrict__ slab_len, int* __restrict__ skipped) {
+                          int nslab, const float* __restrict__ pred, const float* __restrict__ feat,
+                          float margin, float log_thr, const int* __restrict__ slab_len,
+                          int* __restrict__ skipped) {
   const int t = blockIdx.x;
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
   const int cnt = counts[t];
   int* list = tasks + static_cast<long long>(t) * nslab;
   const float* pr = pred + static_cast<long long>(t) * nslab;
+  // scale of the tile: the largest log10 norm-product bound of its tasks
+  float lb = -1e30f;
+  for (int i = lane; i < cnt; i += 32)
+    lb = fmaxf(lb, feat[(static_cast<long long>(t) * nslab + i) * F + 7]);
+  for (int o = 16; o > 0; o >>= 1) lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+  // skip below thr * min(1, bound scale of the tile)
+  const float cut = log_thr + fminf(0.f, lb);
   int out = 0;
   long long ksum = 0;
   for (int base = 0; base < cnt; base += 32) {
     const int i = base + lane;
     const bool in = i < cnt;
     const int s = in ? list[i] : 0;
-    const bool keep = in && (pr[i] + margin >= log_thr);
+    const bool keep = in && (pr[i] + margin >= cut);
     const unsigned mk = __ballot_sync(0xffffffffu, keep);
     __syncwarp();
     if (keep) {
@@ -365,9 +373,10 @@ void mlp_round(const float* theta, void* wb, cudaStream_t st) {
 }
 
 void mlp_compact(int* tasks, int* counts, long long* kacc, int ntiles, int nslab, const float* pred,
-                 float margin, float log_thr, const int* slab_len, int* skipped, cudaStream_t st) {
-  mlp::k_compact<<<ntiles, 32, 0, st>>>(tasks, counts, kacc, nslab, pred, margin, log_thr, slab_len,
-                                        skipped);
+                 const float* feat, float margin, float log_thr, const int* slab_len, int* skipped,
+                 cudaStream_t st) {
+  mlp::k_compact<<<ntiles, 32, 0, st>>>(tasks, counts, kacc, nslab, pred, feat, margin, log_thr,
+                                        slab_len, skipped);
 }
 
 }  // namespace gw

@@ -30,7 +30,11 @@ void mlp_backward(const void* wb, const float* x, const float* z1, const float* 
 void mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, void* wb,
               cudaStream_t st);
 void mlp_round(const float* theta, void* wb, cudaStream_t st);
+// Drop from each tile's list the tasks whose prediction + margin is below
+// log_thr + min(0, largest log10 norm-product bound among the tile's tasks)
+// (feat: [tiles][nslab][kMlpFeatures], the bound is feature 7).
 void mlp_compact(int* tasks, int* counts, long long* kacc, int ntiles, int nslab, const float* pred,
-                 float margin, float log_thr, const int* slab_len, int* skipped, cudaStream_t st);
+                 const float* feat, float margin, float log_thr, const int* slab_len, int* skipped,
+                 cudaStream_t st);
 
 }  // namespace gw

@@ -60,3 +60,29 @@ def test_injected_allocation_failure_and_context_recovers(pkg):
         assert "injected" in str(e.value)
         got = ctx.chi_tau(case.thr, "fp64").cpu().numpy()
     assert _rel(got, ref) <= 1e-10
+
+
+def test_allocation_failure_during_panel_rebuild_leaves_no_stale_cache(pkg):
+    """An injected allocation failure while the 3c panels are rebuilt for a new
+    threshold must not leave them cached under the old one: the next calls
+    with the old threshold (the regular and the allocation-free entry point)
+    rebuild and match the oracle."""
+    from paper_2104_09857_gb300 import _lib
+
+    thr1 = 1e-3
+    case = make_case("ribbon28", n_tau=2)
+    ref = oc.chi_dense(case, thr=thr1)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        assert _rel(ctx.chi_tau(thr1, "fp64").cpu().numpy(), ref) <= 1e-10
+        # thr 0 keeps more 3c blocks than thr1: the rebuild needs a larger
+        # host-table buffer, whose allocation is the injected failure
+        ctx.set_option("test_fail_alloc", 1)
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_tau(0.0, "fp64")
+        assert e.value.code == -5  # GW_ERR_OOM
+        got = ctx.chi_tau(thr1, "fp64").cpu().numpy()
+        assert _rel(got, ref) <= 1e-10
+        out = torch.full((ctx.nri, ctx.nri), float("nan"), dtype=torch.float64, device="cuda:0")
+        _lib.gw_chi_tau_noalloc(ctx.ctx, 1, thr1, out.data_ptr())
+        assert _rel([out.cpu().numpy()], [ref[1]]) <= 1e-10

@@ -97,6 +97,28 @@ def test_qp_rejects_bad_input(pkg):
         with pytest.raises(_lib.GwError) as e:
             _lib.gw_qp_g0w0(ctx.ctx, sig, [0.1, 0.2, 0.5], w, w, [np.nan], [0.0], [0.0])
         assert e.value.code == -4
+        # the first frequency is checked like the others
+        for om in ([0.0, 0.2, 0.5], [-0.1, 0.2, 0.5]):
+            with pytest.raises(_lib.GwError) as e:
+                _lib.gw_qp_g0w0(ctx.ctx, sig, om, w, w, [0.0], [0.0], [0.0])
+            assert e.value.code == -1
+
+
+def test_qp_reports_a_newton_solve_that_does_not_converge(pkg):
+    """A self-energy that is the same at every frequency point leaves the
+    continued fraction's third coefficient 0/0: the Newton solve meets a
+    non-finite value and the call says so (GW_ERR_NOT_CONVERGED) instead of
+    returning the iterate as an energy."""
+    from paper_2104_09857_gb300 import _lib
+
+    sig = np.ones((1, 1, 2))              # S+ = S- = 1 on one tau point
+    gamma = np.full((4, 1), 0.2)          # Sigma(i omega_k) = 0.2 for every k
+    sw = np.zeros((4, 1))
+    with pkg.Context(0) as ctx:
+        with pytest.raises(_lib.GwError) as e:
+            _lib.gw_qp_g0w0(ctx.ctx, sig, [0.1, 0.3, 0.7, 1.5], gamma, sw, [0.0], [0.0], [0.0])
+        assert e.value.code == -10
+        assert "did not converge" in str(e.value)
 
 
 @pytest.mark.parametrize("name,precision,tol", [("benzene", "fp64", 1e-10), ("ribbon28", "fp64", 1e-10),

@@ -1,5 +1,6 @@
 """The allocation-free chi entry point (gw_chi_tau_noalloc) against the
-regular one (gw_chi_tau, FP64), called twice in a row through the C ABI.
+regular one (gw_chi_tau, FP64) and against the CPU oracle, called twice in a
+row through the C ABI, with the device's free memory unchanged across calls.
 
 It exists for callers that cannot call cudaMalloc when they need chi (a host
 framework whose caching allocator owns the device memory budget, a process
@@ -16,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+from oracle import chi as oc  # noqa: E402
 from synth import make_case  # noqa: E402
 
 TOL = 1e-10  # the FP64 tolerance of the parity tests
@@ -42,18 +44,25 @@ def test_noalloc_matches_chi_tau_twice(pkg, name, thr):
     from paper_2104_09857_gb300 import _lib
 
     case = make_case(name, n_tau=4)
+    oracle = oc.chi_dense(case, thr=thr)
     with pkg.Context(0) as ctx:
         ctx.load_case(case)
         ref = ctx.chi_tau(thr, "fp64").cpu().numpy()
         out = torch.full((ctx.nri, ctx.nri), float("nan"), dtype=torch.float64, device="cuda:0")
+        _lib.gw_chi_tau_noalloc(ctx.ctx, 0, thr, out.data_ptr())  # first call: address look-up
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(0)[0]
         for j in (1, 2):
             for _ in range(2):
                 _lib.gw_chi_tau_noalloc(ctx.ctx, j, thr, out.data_ptr())
                 got = out.cpu().numpy()
                 assert np.all(np.isfinite(got))
-                assert _rel(got, ref[j]) <= TOL
-                assert np.abs(got - ref[j]).max() <= TOL * np.abs(ref[j]).max()
+                for want in (ref[j], oracle[j]):
+                    assert _rel(got, want) <= TOL
+                    assert np.abs(got - want).max() <= TOL * np.abs(want).max()
                 out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info(0)[0] == free0, "device memory was allocated"
 
 
 def test_noalloc_requires_panels_and_rejects_bad_arguments(pkg):

@@ -57,7 +57,8 @@ def test_evgw_matches_oracle_and_restores_levels(pkg):
         got, cycles = _lib.gw_evgw(ctx.ctx, vc, omega, gamma, delta, s, orbs, sx, case.thr,
                                    _lib.GW_FP64, 20, 1e-8)
         chi = ctx.chi_tau(case.thr, "fp64", 0, 1).cpu().numpy()
-    print(f"evGW HOMO/LUMO {got} after {cycles} cycles; oracle {ref} after {ref_cycles}")
+    print(f"evGW HOMO/LUMO {got} after {cycles} cycles; oracle {ref} after {ref_cycles}; "
+          f"max |difference| {np.max(np.abs(got - ref)):.3e} Ha")
     assert abs(cycles - ref_cycles) <= 1
     assert np.max(np.abs(got - ref)) < 1e-6
     # the context is back on the levels given to gw_set_greens

@@ -11,10 +11,15 @@ value  = useful TFLOP/s of the mixed-precision form (default FP16x3: two scaled
          binary16 slices, 3 tensor-core products; flops of the surviving
          atom-block products of Eq. 3's steps A, B, C; split products,
          padding and skipped work not counted), whole job.
-Also reported: ms per tau point, the FP64 form on a subset of tau points,
-the rooflines of the two tensor-core kernels (steps A/B and step C), a
-sampled error against the FP64 block oracle, an end-to-end figure through
-host buffers, and the CPU oracle on a bounded sample.
+Also reported: ms per tau point; the other forms (FP64, FP32, BF16x3,
+BF16x6) on one tau point with their sampled errors; the rooflines of the two
+tensor-core kernels (steps A/B and step C) against the measured tensor peak,
+and of the CUDA-core forms against the FFMA/DFMA throughput measured here
+(--peaks prints those alone); the error of the timed form against the FP64
+block oracle at every tau point; the learned screen at the same threshold
+(time, skipped tasks, error); an end-to-end figure through host buffers; and
+the CPU oracle on a bounded sample, whose useful flops are the oracle's own
+count (tests/golden/flops_ribbon298.json).
 
 Multi-GPU: tau points are independent; rank r takes steps r, r + N, ... of
 the tau cycle (no collective on the data path): weak scaling.
@@ -34,7 +39,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "ribbon300"
-FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 lanes x 2 flop x max SM clock
 N_PRODUCTS = {"fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3, "fp64": 1}
 SPLIT_FORMS = ("bf16x3", "bf16x6", "fp16x3")
 
@@ -188,7 +192,7 @@ def run_reference(args):
     from synth import make_case
 
     case = make_case(WORKLOAD)
-    flops_tau = _useful_flops_oracle_side(case)
+    flops_tau = _useful_flops_oracle_side(case, len(case.tau) // 2)
     for _ in range(args.warmup):
         cpu_oracle_sample(case, 1, flops_tau)
     t0 = time.perf_counter()
@@ -210,36 +214,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _useful_flops_oracle_side(case) -> float:
-    """Useful flops of one tau point counted from the stored 3c blocks alone,
-    for a tau at which no Green's-function block is filtered (true for this
-    workload away from the largest tau): steps A and B do
-    2 nao n_l n_s n_P per stored block orientation; step C does
-    2 n_m n_s n_p n_q for every (m, s, p <= q) with p in the RI window of s
-    and q in the RI window of m (the windows of nonzero intermediates)."""
-    import numpy as np
-
-    s = case.system
-    t3 = case.t3c
-    blk = t3.blocks
-    na = s.n_ao[blk[:, 0]].astype(float)
-    nb = s.n_ao[blk[:, 1]].astype(float)
-    npp = s.n_ri[blk[:, 2]].astype(float)
-    w = na * nb * npp * np.where(blk[:, 0] == blk[:, 1], 1.0, 2.0)
-    fa = 2.0 * s.nao_total * w.sum()
-    n_at = s.n_atoms
-    win = np.zeros((n_at, n_at), dtype=bool)
-    win[blk[:, 0], blk[:, 2]] = True
-    win[blk[:, 1], blk[:, 2]] = True
-    x = win * s.n_ri[None, :].astype(float)            # x[s, p]
-    ysuf = np.cumsum(x[:, ::-1], axis=1)[:, ::-1]      # ysuf[m, p] = sum_{q >= p} x[m, q]
-    pairs = x @ ysuf.T                                 # [s, m]
-    nao = s.n_ao.astype(float)
-    fc = 2.0 * float(nao @ pairs @ nao)
-    return 2.0 * fa + fc
+def _useful_flops_oracle_side(case, tau_index: int) -> float:
+    """Useful flops of one tau point as the oracle counts them from its own
+    filtered blocks (oracle.chi.useful_flops_blocks; the flops of the atom-block
+    products whose operands survive the filter), read from the count that
+    tests/golden/make_flops_ribbon298.py wrote for the benchmark workload."""
+    path = os.path.join(ROOT, "tests", "golden", "flops_ribbon298.json")
+    with open(path) as f:
+        rec = json.load(f)["per_tau"][str(tau_index)]
+    return rec["flops_a"] + rec["flops_b"] + rec["flops_c"]
 
 
-def _roof(flops, seconds, prec, peaks, peak_src, kernel, traffic):
+def alu_peaks():
+    """Measured FFMA and DFMA throughput of this GPU (libgwpeaks.so), TFLOP/s."""
+    import ctypes
+
+    from paper_2104_09857_gb300 import build as b
+
+    lib = ctypes.CDLL(b.build_peaks())
+    lib.gw_fma_peak.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, fp64, iters in (("fp32", 0, 20000), ("fp64", 1, 400)):
+        tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        rc = lib.gw_fma_peak(fp64, iters, ctypes.byref(tf), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError(f"gw_fma_peak({name}) failed: {rc}")
+        out[name] = {"tflops": tf.value, "ms": ms.value, "iters": iters}
+    out["how"] = ("FMA chains, 8 independent per thread, 8 CTAs x 256 threads per SM, best of "
+                  "3 launches timed with CUDA events (paper_2104_09857_gb300/peaks/fma_peaks.cu)")
+    return out
+
+
+def _roof(flops, seconds, prec, peaks, peak_src, kernel, traffic, alu=None):
     """Roofline object of one kernel: achieved = useful flops / its device
     time over the timed region (the same per average launch)."""
     achieved = flops / seconds / 1e12 if seconds > 0 else None
@@ -250,8 +257,9 @@ def _roof(flops, seconds, prec, peaks, peak_src, kernel, traffic):
                 f"product")
         bound = "tensor"
     else:
-        peak = FFMA_PEAK_TFLOPS if prec == "fp32" else None
-        note = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if peak else "FP64 ALU"
+        peak = alu[prec]["tflops"] if alu else None
+        note = (f"measured {'FFMA' if prec == 'fp32' else 'DFMA'} throughput of this GPU "
+                f"(libgwpeaks)") if peak else "not measured"
         bound = "alu"
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if (achieved and peak) else None,
@@ -276,6 +284,58 @@ def _traffic(prec):
     return {"ab": rec.get("panel_job_bytes_per_launch"), "c": rec.get("chi_job_bytes_per_launch")}
 
 
+def _block_errors(got_blocks, ref_blocks):
+    """(relative Frobenius error, element error over max |ref|) of a sample."""
+    import numpy as np
+
+    num = sum(float(np.sum((g - r) ** 2)) for g, r in zip(got_blocks, ref_blocks))
+    den = sum(float(np.sum(r ** 2)) for r in ref_blocks)
+    emax = max(float(np.abs(g - r).max()) for g, r in zip(got_blocks, ref_blocks))
+    rmax = max(float(np.abs(r).max()) for r in ref_blocks)
+    return ((num / den) ** 0.5 if den > 0 else None), (emax / rmax if rmax > 0 else None)
+
+
+def _diag_blocks(chi2d, ri, atoms):
+    return [chi2d[ri[p]:ri[p + 1], ri[p]:ri[p + 1]].cpu().numpy() for p in atoms]
+
+
+def _train_screen(Context, device, thr, precision):
+    """Train the learned screen on task logs of the benzene ring (the first
+    configuration) and two short ribbons of the benchmark's family, and
+    calibrate its margin on held-out tasks.  Returns (params, margin, info)."""
+    import numpy as np
+
+    from paper_2104_09857_gb300 import _lib
+    from synth import make_case
+
+    feats, tgts = [], []
+    for name, nt in (("benzene", 6), ("ribbon28", 4), ("ribbon60", 3)):
+        c = make_case(name, n_tau=nt, thr=1e-9)
+        with Context(device) as lc:
+            lc.load_case(c)
+            f, t = _lib.gw_mlp_log(lc.ctx, 0, nt, thr, _lib.PRECISIONS[precision])
+        feats.append(f)
+        tgts.append(t)
+    x = np.concatenate(feats)
+    y = np.concatenate(tgts)
+    keep = y > -39.0
+    x, y = x[keep], y[keep]
+    idx = np.random.default_rng(3).permutation(len(y))
+    n_tr = int(0.8 * len(y))
+    tr, va = idx[:n_tr], idx[n_tr:]
+    with Context(device) as tc:
+        _lib.gw_mlp_init(tc.ctx, 17)
+        t0 = time.perf_counter()
+        losses = _lib.gw_mlp_train(tc.ctx, x[tr], y[tr], epochs=400, batch=0, lr=3e-3, seed=5)
+        t_train = time.perf_counter() - t0
+        pv = _lib.gw_mlp_predict(tc.ctx, x[va])
+        params = _lib.gw_mlp_get_params(tc.ctx)
+    margin = float(np.max(y[va] - pv)) + 0.25
+    return params, margin, {"samples": int(len(y)), "loss_first": float(losses[0]),
+                            "loss_last": float(losses[-1]), "train_s": t_train,
+                            "margin": margin, "trained_on": "benzene, ribbon28, ribbon60 task logs"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -293,6 +353,7 @@ def run_ours(args):
     from synth import make_case
 
     peaks, peak_src = _peaks()
+    alu = alu_peaks() if args.alu_peaks else None
     prec = args.precision
     t_gen = time.perf_counter()
     case = make_case(args.workload)
@@ -306,8 +367,11 @@ def run_ours(args):
     nri = ctx.nri
     out = torch.empty((1, nri, nri), dtype=torch.float64, device=f"cuda:{local}")
 
-    def step(j, precision):
-        ctx.chi_tau(case.thr, precision, j, 1, out=out)
+    def step(j, precision, screening=None):
+        if screening is None:
+            ctx.chi_tau(case.thr, precision, j, 1, out=out)
+        else:
+            ctx.chi_tau(case.thr, precision, j, 1, out=out, screening=screening)
         return ctx.stats()
 
     # warm-up (W steps on the first tau points of this rank's cycle)
@@ -343,10 +407,13 @@ def run_ours(args):
     # PanelJob, two launches per batch) and step C (ChiJob, one per batch);
     # "roofline" is the one that takes more time
     traffic = _traffic(prec)
+    nb = max(1, agg["n_batches"])
     roof_ab = _roof(agg["flops_a"] + agg["flops_b"], agg["ms_step_ab"] / 1e3, prec, peaks, peak_src,
-                    "steps A/B (panel job; time includes the two G gathers)", traffic.get("ab"))
+                    "steps A/B (panel job; time includes the two G gathers)", traffic.get("ab"), alu)
     roof_c = _roof(agg["flops_c"], agg["ms_step_c_kernel"] / 1e3, prec, peaks, peak_src,
-                   "step C (chi job)", traffic.get("c"))
+                   "step C (chi job)", traffic.get("c"), alu)
+    for r, n_l in ((roof_ab, 2 * nb), (roof_c, nb)):
+        r["launches"] = n_l
     if agg["ms_step_ab"] >= agg["ms_step_c_kernel"]:
         roof, roof_other = roof_ab, roof_c
     else:
@@ -374,25 +441,102 @@ def run_ours(args):
         "gpu_launches": int(agg["kernel_launches"]),
         "clocks": clk,
     }
+    if alu:
+        result["alu_peaks"] = alu
 
-    if rank == 0 and world == 1:
-        # FP64 form on a subset of tau points
-        if args.fp64_taus > 0:
-            f_fl, f_ms = 0.0, 0.0
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            for i in range(args.fp64_taus):
-                j = (n_tau // 2 + i) % n_tau
+    if rank == 0 and world == 1 and args.workload == WORKLOAD:
+        from oracle import chi as oc
+
+        ri = np.concatenate([[0], np.cumsum(case.system.n_ri)])
+        jm = n_tau // 2
+        # CPU oracle on a bounded sample of tau index jm; its diagonal blocks
+        # are the sample every form below is checked on
+        flops_oracle = _useful_flops_oracle_side(case, jm)
+        res = cpu_oracle_sample(case, args.cpu_samples, flops_oracle)
+        result["cpu_baseline"] = {k: v for k, v in res.items()
+                                  if k not in ("sample_seconds", "tau_index", "blocks")}
+        atoms_m = sorted(res["blocks"])
+        refs_m = [res["blocks"][p] for p in atoms_m]
+        # every form at tau index jm: time, useful TFLOP/s, sampled error
+        forms = {}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for form in args.forms.split(","):
+            if not form:
+                continue
+            step(jm, form)  # first call of a form builds its operands
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = step(jm, form)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f_ms = e0.elapsed_time(e1)
+            rel, el = _block_errors(_diag_blocks(out[0], ri, atoms_m), refs_m)
+            forms[form] = {"ms_per_tau": f_ms, "useful_tflops": st["flops_useful"] / f_ms / 1e9,
+                           "rel_frobenius": rel, "rel_element": el,
+                           "roofline_step_c": _roof(st["flops_c"], st["ms_step_c_kernel"] / 1e3, form,
+                                                    peaks, peak_src, "step C", None, alu)}
+            if form == "fp64":
+                forms[form]["speedup_timed_form_over_fp64"] = f_ms / ms_per_tau
+        forms["tau_index"] = jm
+        forms["sample"] = f"diagonal chi blocks of RI atoms {atoms_m} at tau index {jm}"
+        forms["useful_flops_library"] = st["flops_useful"]
+        forms["useful_flops_oracle"] = flops_oracle
+        result["forms"] = forms
+        # per-tau parity of the timed form: one diagonal block per tau point
+        # (atom a_j of a seeded permutation), oracle M and N slices each
+        bo = oc.BlockOracle(case)
+        perm = np.random.default_rng(20210420).permutation(case.system.n_atoms)
+        per_tau, oracle_blocks = [], {}
+        for j in range(min(args.parity_taus, n_tau)):
+            a = int(perm[j])
+            ref = bo.block(j, a, a, {})
+            oracle_blocks[j] = (a, ref)
+            step(j, prec)
+            torch.cuda.synchronize()
+            rel, el = _block_errors(_diag_blocks(out[0], ri, [a]), [ref])
+            per_tau.append({"tau_index": j, "atom": a, "rel_frobenius": rel, "rel_element": el})
+        result["parity"] = {"form": prec, "reference": "numpy FP64 block oracle", "per_tau": per_tau,
+                            "max_rel_frobenius": max(p["rel_frobenius"] for p in per_tau),
+                            "max_rel_element": max(p["rel_element"] for p in per_tau)}
+        # learned screening at the bench threshold: time, skipped tasks,
+        # per-tau error on the same oracle blocks
+        if args.learned:
+            params, margin, info = _train_screen(Context, local, case.thr, prec)
+            from paper_2104_09857_gb300 import _lib
+
+            _lib.gw_mlp_set_params(ctx.ctx, params)
+            ctx.set_option("mlp_margin", margin)
+            lt = []
+            l_ms = 0.0
+            skipped = seen = 0
+            fl_u = fl_i = fl_i_plain = 0.0
+            for j in range(n_tau):
+                st_plain = step(j, prec)
+                fl_i_plain += st_plain["flops_issued"]
+                torch.cuda.synchronize()
                 e0.record(stream)
-                st = step(j, "fp64")
+                st = step(j, prec, screening=_lib.GW_SCREEN_MLP)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                f_ms += e0.elapsed_time(e1)
-                f_fl += st["flops_useful"]
-            result["fp64"] = {"ms_per_tau": f_ms / args.fp64_taus,
-                              "useful_tflops": f_fl / (f_ms / 1e3) / 1e12,
-                              "taus_timed": args.fp64_taus,
-                              "speedup_mixed_over_fp64": (f_ms / args.fp64_taus) / ms_per_tau}
+                l_ms += e0.elapsed_time(e1)
+                skipped += st["tasks_skipped"]
+                seen += st["tasks_seen"]
+                fl_u += st["flops_useful"]
+                fl_i += st["flops_issued"]
+                if j in oracle_blocks:
+                    a, ref = oracle_blocks[j]
+                    rel, el = _block_errors(_diag_blocks(out[0], ri, [a]), [ref])
+                    lt.append({"tau_index": j, "rel_frobenius": rel, "rel_element": el})
+            result["learned"] = {
+                "ms_per_tau": l_ms / n_tau, "ms_per_tau_norm_bound": ms_per_tau,
+                "tasks_skipped": skipped, "tasks_seen": seen,
+                "skipped_fraction": skipped / seen if seen else None,
+                "flops_issued_fraction": fl_i / fl_i_plain if fl_i_plain else None,
+                "useful_tflops_credited": fl_u / (l_ms / 1e3) / 1e12 if l_ms else None,
+                "per_tau": lt,
+                "max_rel_frobenius": max((p["rel_frobenius"] for p in lt), default=None),
+                "training": info}
         # end to end through host buffers: upload inputs, chi, download
         if args.e2e_steps > 0:
             t3 = case.t3c
@@ -417,29 +561,6 @@ def run_ours(args):
                                                        case.tau.nbytes),
                              "d2h_bytes_per_step": int(nri * nri * 8),
                              "ms_per_step": t_e * 1e3 / args.e2e_steps}
-        # CPU oracle, bounded sample; its diagonal chi blocks also give a
-        # sampled error of the timed form at that tau point
-        if args.cpu_samples > 0:
-            per_tau = flops_job / max(1, args.steps * world)
-            res = cpu_oracle_sample(case, args.cpu_samples, per_tau)
-            result["cpu_baseline"] = {k: v for k, v in res.items()
-                                      if k not in ("sample_seconds", "tau_index", "blocks")}
-            step(res["tau_index"], prec)
-            torch.cuda.synchronize()
-            ri = np.concatenate([[0], np.cumsum(case.system.n_ri)])
-            num = den = 0.0
-            emax = rmax = 0.0
-            for p, ref in res["blocks"].items():
-                got = out[0, ri[p]:ri[p + 1], ri[p]:ri[p + 1]].cpu().numpy()
-                num += float(np.sum((got - ref) ** 2))
-                den += float(np.sum(ref ** 2))
-                emax = max(emax, float(np.abs(got - ref).max()))
-                rmax = max(rmax, float(np.abs(ref).max()))
-            result["parity"] = {"form": prec, "tau_index": res["tau_index"],
-                                "blocks": [[int(p), int(p)] for p in res["blocks"]],
-                                "rel_frobenius": (num / den) ** 0.5 if den > 0 else None,
-                                "rel_element": emax / rmax if rmax > 0 else None,
-                                "reference": "numpy FP64 block oracle"}
         result["setup"] = {"generate_s": t_gen}
     ctx.close()
     if rank == 0:
@@ -456,14 +577,29 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "bf16x3", "bf16x6", "fp16x3", "fp64"],
                     default="fp16x3")
-    ap.add_argument("--fp64-taus", type=int, default=1)
+    ap.add_argument("--forms", default="fp64,fp32,bf16x3,bf16x6",
+                    help="other forms timed on one tau point and checked on the oracle sample")
+    ap.add_argument("--parity-taus", type=int, default=20,
+                    help="tau points of the timed form checked against the oracle (one block each)")
+    ap.add_argument("--learned", type=int, default=1,
+                    help="train the learned screen and time it on every tau point")
+    ap.add_argument("--alu-peaks", type=int, default=1,
+                    help="measure the FFMA/DFMA throughput the FP32/FP64 rooflines divide by")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only measure and print the FFMA/DFMA throughput of this GPU")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-samples", type=int, default=1)
+    ap.add_argument("--cpu-samples", type=int, default=2)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic case (smaller ones serve profiling); the bench line is %(default)s")
     ap.add_argument("--batch-atoms", type=int, default=0,
                     help="upper limit on sigma-atoms per operand batch (0: byte budget only)")
     args = ap.parse_args()
+    if args.peaks:
+        import __graft_entry__ as g
+
+        g.build()
+        print(json.dumps(alu_peaks()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

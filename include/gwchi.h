@@ -83,6 +83,8 @@ typedef struct gw_stats {
   int n_batches;
   long long tasks_seen;    /* learned screening: step-C tasks examined            */
   long long tasks_skipped; /* learned screening: tasks dropped by the prediction  */
+  long long batches_skipped; /* operand batches whose X or Y was entirely
+                              filtered (their contribution to chi is zero) */
 } gw_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -198,9 +200,10 @@ int gw_chi_to_w(gw_ctx* ctx, const double* V, int n_omega, const double* gamma,
  * global memory inside the library (held on each GPU that loads the library
  * until the process exits).  Systems whose Green's functions, chi and the
  * operands of one single-sigma-atom batch do not fit are rejected with
- * GW_ERR_INVALID_ARG and a message giving the bytes needed.  The tensor
- * panels depend on thr and are built by gw_chi_tau: call it once with the same
- * thr first (GW_ERR_ORDER otherwise).  The first call on a device looks up
+ * GW_ERR_INVALID_ARG and a message giving the bytes needed.  The FP64 tensor
+ * panels depend on thr and are built by gw_chi_tau on its CUDA-core routes:
+ * call it once with the same thr and precision GW_FP64 (or GW_FP32) first
+ * (GW_ERR_ORDER otherwise).  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture begins.  Each call copies its small per-batch
  * tables from pageable host memory and synchronises the context's stream
@@ -388,6 +391,11 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
  *                  (default 40e9)
  *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)
+ *   "mu_chunk_atoms" split forms: mu-atoms per chunk of the 2-D operand
+ *                  batches (0 = automatic: the fewest equal chunks for which
+ *                  one sigma-atom's X and Y fit in batch_bytes / 8; one chunk
+ *                  keeps Y over every RI function, several give each chunk
+ *                  the RI window of its atoms' 3c blocks)
  *   "flush_k"      split forms: reduction elements between drains of the
  *                  tensor cores' main FP32 accumulator (rounded down to a
  *                  multiple of 16, default 64; each 16-element MMA step of the

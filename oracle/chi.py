@@ -368,3 +368,87 @@ class BlockOracle:
         nn = n[:, idx_p]                  # [|idx_q|, |idx_p|, nQ]
         kk = mm.shape[0] * mm.shape[1]
         return -(mm.reshape(kk, -1).T @ nn.reshape(kk, -1))
+
+
+# ----------------------------------------------------------------------------
+# useful work of one tau point (the flops the method must do after filtering)
+# ----------------------------------------------------------------------------
+
+def _count_c(n_ao, n_ri, keep_m, keep_n) -> float:
+    """F_C = sum over (mu-atom m, sigma-atom s) and RI atoms p <= q of
+    2 n(m) n(s) n(p) n(q), for kept nonzero M(m, s, p) and N(m, s, q)."""
+    nao = np.asarray(n_ao, dtype=float)
+    nri = np.asarray(n_ri, dtype=float)
+    xm = keep_m * nri[None, None, :]                         # [m, s, p]
+    xn = keep_n * nri[None, None, :]                         # [m, s, q]
+    suffix = np.cumsum(xn[:, :, ::-1], axis=2)[:, :, ::-1]   # sum over q >= p
+    per_pair = np.sum(xm * suffix, axis=2)                   # [m, s]
+    return float(2.0 * nao @ per_pair @ nao)
+
+
+def _count_ab(case, thr, keep_go, keep_gv):
+    """(F_A, F_B): every stored T block orientation (lambda-atom, sigma-atom,
+    P) that survives the T filter, times every kept G block (mu-atom,
+    lambda-atom): 2 n(mu) n(lambda) n(sigma) n(P) flops (G^occ for step A,
+    G^virt for step B)."""
+    s = case.system
+    blk = case.t3c.blocks
+    fa = fb = 0.0
+    for i, (a, b, p) in enumerate(blk):
+        d = case.t3c.data[case.t3c.offsets[i]:case.t3c.offsets[i + 1]]
+        if thr > 0.0 and np.sqrt(np.sum(d * d)) < thr:
+            continue
+        w = 2.0 * s.n_ao[a] * s.n_ao[b] * s.n_ri[p]
+        for lam in ((a,) if a == b else (a, b)):
+            fa += w * float(s.n_ao @ keep_go[:, lam])
+            fb += w * float(s.n_ao @ keep_gv[:, lam])
+    return fa, fb
+
+
+def _g_keep(g, ao, thr):
+    """Kept nonzero atom blocks of a filtered symmetric G (thr 0 keeps all)."""
+    if thr <= 0.0:
+        return np.ones((len(ao) - 1, len(ao) - 1), dtype=bool)
+    return np.sqrt(block_sq_sums(filter_sym_2d(g, ao, thr), [ao, ao])) > 0.0
+
+
+def useful_flops_dense(case, tau_index: int, thr: float | None = None):
+    """(F_A, F_B, F_C) of one tau point from the dense route (small systems):
+    the flops of the atom-block products of Eq. 3 whose operands survive the
+    filter (kept and nonzero), each product counted once; chi's atom-block
+    upper triangle p <= q for step C."""
+    sysm = case.system
+    thr = case.thr if thr is None else thr
+    ao, ri = offsets(sysm.n_ao), offsets(sysm.n_ri)
+    t = dense_three_center(sysm.n_ao, sysm.n_ri, case.t3c.blocks, case.t3c.offsets,
+                           case.t3c.data, thr)
+    go, gv = greens(case.C, case.eps, case.n_occ, case.mu_fermi, case.tau[tau_index])
+    go, gv = filter_sym_2d(go, ao, thr), filter_sym_2d(gv, ao, thr)
+    m = filter_3idx(np.einsum("ml,lsp->msp", go, t, optimize=True), [ao, ao, ri], thr)
+    n = filter_3idx(np.einsum("mnq,ns->msq", t, gv, optimize=True), [ao, ao, ri], thr)
+    keep_m = np.sqrt(block_sq_sums(m, [ao, ao, ri])) > 0.0
+    keep_n = np.sqrt(block_sq_sums(n, [ao, ao, ri])) > 0.0
+    fa, fb = _count_ab(case, thr, _g_keep(go, ao, thr), _g_keep(gv, ao, thr))
+    return fa, fb, _count_c(sysm.n_ao, sysm.n_ri, keep_m, keep_n)
+
+
+def useful_flops_blocks(bo: BlockOracle, tau_index: int):
+    """(F_A, F_B, F_C) of one tau point from the block oracle's M and N slices
+    (large systems): the same count as useful_flops_dense."""
+    n_at = len(bo.n_ao)
+    keep_m = np.zeros((n_at, n_at, n_at), dtype=bool)
+    keep_n = np.zeros((n_at, n_at, n_at), dtype=bool)
+    for p in range(n_at):
+        idx, m = bo.m_slice(tau_index, p)
+        _, atoms, _ = bo.t_slice(p)
+        cuts = bo._atom_cuts(atoms)
+        nm = np.add.reduceat(np.add.reduceat(np.sum(m * m, axis=2), bo.ao[:-1], axis=0),
+                             cuts[:-1], axis=1)
+        keep_m[:, atoms, p] = nm > 0.0
+        idx, n = bo.n_slice(tau_index, p)
+        nn = np.add.reduceat(np.add.reduceat(np.sum(n * n, axis=2), cuts[:-1], axis=0),
+                             bo.ao[:-1], axis=1)
+        keep_n[atoms, :, p] = nn > 0.0
+    go, gv = bo.greens(tau_index)
+    fa, fb = _count_ab(bo.case, bo.thr, _g_keep(go, bo.ao, bo.thr), _g_keep(gv, bo.ao, bo.thr))
+    return fa, fb, _count_c(bo.n_ao, bo.n_ri, keep_m, keep_n)

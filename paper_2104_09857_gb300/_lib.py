@@ -67,6 +67,7 @@ class gw_stats(ctypes.Structure):
         ("n_batches", ctypes.c_int),
         ("tasks_seen", ctypes.c_longlong),
         ("tasks_skipped", ctypes.c_longlong),
+        ("batches_skipped", ctypes.c_longlong),
     ]
 
     def as_dict(self) -> dict:

@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgwchi.so")
+# the FFMA/DFMA throughput probe the benchmark's FP32/FP64 rooflines divide by
+PEAKS_SRC = os.path.join(HERE, "peaks", "fma_peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libgwpeaks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -50,7 +53,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def build_peaks(force: bool = False) -> str:
+    """libgwpeaks.so: the FMA throughput probe (one translation unit)."""
+    if (not force and os.path.exists(PEAKS_LIB)
+            and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC)):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + ".tmp"
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-shared", PEAKS_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
+    build_peaks(force)
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()

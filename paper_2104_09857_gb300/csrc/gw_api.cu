@@ -139,6 +139,7 @@ void reset_tensor(gw_ctx* ctx) {
   ctx->blk.clear();
   ctx->blk_off.clear();
   ctx->blk_norm.clear();
+  ctx->plan_ok = false;
   ctx->panels_ok = false;
   ctx->panel32_ok = false;
   free_dev(ctx->d_pt);
@@ -163,17 +164,23 @@ struct Timer {
 // ---------------------------------------------------------------------------
 // panels
 // ---------------------------------------------------------------------------
-int build_panels(gw_ctx* ctx, double thr) {
-  if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
-  // the cached panels (and everything derived from them) stop being valid
-  // here: an allocation or copy below may fail and leave the pool half built
+// Host plan of the owner panels for threshold thr: which 3c blocks survive
+// the filter, each owner's lambda atoms and RI window, and where each kept
+// block lands in the two panels it belongs to.  Uploads the lambda lists.
+int plan_panels(gw_ctx* ctx, double thr) {
+  if (ctx->plan_ok && ctx->plan_thr == thr) return GW_OK;
+  // everything derived from an earlier plan stops being valid here: an
+  // allocation or copy below may fail and leave it half built
+  ctx->plan_ok = false;
+  ctx->plan_thr = -1.0;
   ctx->panels_ok = false;
   ctx->panels_thr = -1.0;
   ctx->pt_ok = false;
   ctx->panel32_ok = false;
   ctx->ycov_valid = false;
   const int n = ctx->n_at;
-  std::vector<int> kept;
+  std::vector<int>& kept = ctx->plan_kept;
+  kept.clear();
   kept.reserve(ctx->n_blocks);
   for (long long b = 0; b < ctx->n_blocks; ++b)
     if (!(ctx->blk_norm[b] < thr)) kept.push_back((int)b);
@@ -193,7 +200,6 @@ int build_panels(gw_ctx* ctx, double thr) {
   }
   ctx->panels.assign(n, PanelDesc{});
   std::vector<int> lam;
-  std::vector<std::vector<int>> rowpos(n);  // rowpos[s][atom] (dense per owner via map)
   std::vector<std::map<int, int>> rowmap(n);
   long long off = 0;
   for (int s = 0; s < n; ++s) {
@@ -221,6 +227,56 @@ int build_panels(gw_ctx* ctx, double thr) {
   }
   ctx->panel_elems = off;
   ctx->lam_total = (long long)lam.size();
+  // flop weights of steps A and B per (owner, lambda-atom)
+  {
+    std::vector<std::map<int, double>> wl(n);
+    for (int b : kept) {
+      const int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
+      const double w = 2.0 * ctx->n_ao[A] * ctx->n_ao[B] * ctx->n_ri[p];
+      wl[B][A] += w;
+      if (A != B) wl[A][B] += w;
+    }
+    ctx->wl_off.assign(n + 1, 0);
+    ctx->wl_atom.clear();
+    ctx->wl_w.clear();
+    for (int s = 0; s < n; ++s) {
+      for (const auto& kv : wl[s]) {
+        ctx->wl_atom.push_back(kv.first);
+        ctx->wl_w.push_back(kv.second);
+      }
+      ctx->wl_off[s + 1] = (int)ctx->wl_atom.size();
+    }
+  }
+  ctx->plan_kB.resize(kept.size());
+  ctx->plan_kA.resize(kept.size());
+  for (size_t i = 0; i < kept.size(); ++i) {
+    const int b = kept[i];
+    const int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1];
+    ctx->plan_kB[i] = rowmap[B][A];
+    ctx->plan_kA[i] = rowmap[A][B];
+  }
+  free_dev(ctx->d_lam);
+  ctx->d_lam = nullptr;
+  GW_TRY(cudaMalloc(&ctx->d_lam, std::max<size_t>(lam.size(), 1) * sizeof(int)));
+  if (!lam.empty())
+    GW_TRY(cudaMemcpy(ctx->d_lam, lam.data(), lam.size() * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->plan_ok = true;
+  ctx->plan_thr = thr;
+  return GW_OK;
+}
+
+// The FP64 owner panels of the plan (the CUDA-core routes, the self-energy
+// and the allocation-free entry point).
+int build_panels(gw_ctx* ctx, double thr) {
+  int rc;
+  if ((rc = plan_panels(ctx, thr))) return rc;
+  if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
+  // the pool (and its FP32 copy) stops being valid until rebuilt below
+  ctx->panels_ok = false;
+  ctx->panels_thr = -1.0;
+  ctx->panel32_ok = false;
+  const std::vector<int>& kept = ctx->plan_kept;
+  const long long off = ctx->panel_elems;
   // destinations of each kept block
   std::vector<long long> dstB(kept.size()), dstA(kept.size());
   std::vector<int> ldB(kept.size()), ldA(kept.size());
@@ -229,36 +285,27 @@ int build_panels(gw_ctx* ctx, double thr) {
     int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
     const PanelDesc& pb = ctx->panels[B];
     ldB[i] = pb.npw * pb.nsig;
-    dstB[i] = pb.off + (long long)rowmap[B][A] * ldB[i] + (long long)(ctx->ri_off[p] - pb.p0) * pb.nsig;
+    dstB[i] = pb.off + (long long)ctx->plan_kB[i] * ldB[i] + (long long)(ctx->ri_off[p] - pb.p0) * pb.nsig;
     const PanelDesc& pa = ctx->panels[A];
     ldA[i] = pa.npw * pa.nsig;
-    dstA[i] = pa.off + (long long)rowmap[A][B] * ldA[i] + (long long)(ctx->ri_off[p] - pa.p0) * pa.nsig;
+    dstA[i] = pa.off + (long long)ctx->plan_kA[i] * ldA[i] + (long long)(ctx->ri_off[p] - pa.p0) * pa.nsig;
   }
   free_dev(ctx->d_panel64);
   free_dev(ctx->d_panel32);
-  free_dev(ctx->d_lam);
   ctx->d_panel64 = nullptr;
   ctx->d_panel32 = nullptr;
-  ctx->d_lam = nullptr;
-  ctx->panel32_ok = false;
   GW_TRY(cudaMalloc(&ctx->d_panel64, std::max<long long>(off, 1) * sizeof(double)));
-  GW_TRY(cudaMalloc(&ctx->d_lam, std::max<size_t>(lam.size(), 1) * sizeof(int)));
   GW_TRY(cudaMemsetAsync(ctx->d_panel64, 0, std::max<long long>(off, 1) * sizeof(double), ctx->stream));
-  if (!lam.empty())
-    GW_TRY(cudaMemcpyAsync(ctx->d_lam, lam.data(), lam.size() * sizeof(int), cudaMemcpyHostToDevice,
-                           ctx->stream));
   int *d_kept, *d_ldB, *d_ldA;
   long long *d_dstB, *d_dstA;
-  int rc;
   if ((rc = upload(ctx, "kept", kept, &d_kept))) return rc;
   if ((rc = upload(ctx, "dstB", dstB, &d_dstB))) return rc;
   if ((rc = upload(ctx, "dstA", dstA, &d_dstA))) return rc;
   if ((rc = upload(ctx, "ldB", ldB, &d_ldB))) return rc;
   if ((rc = upload(ctx, "ldA", ldA, &d_ldA))) return rc;
-  int *d_nao, *d_nri, *d_rioff;
+  int *d_nao, *d_nri;
   if ((rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao))) return rc;
   if ((rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri))) return rc;
-  (void)d_rioff;
   gw::launch_panel_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, ctx->d_ri_off,
                            d_kept, (int)kept.size(), d_dstB, d_dstA, d_ldB, d_ldA, ctx->d_panel64,
                            ctx->stream);
@@ -266,7 +313,6 @@ int build_panels(gw_ctx* ctx, double thr) {
   GW_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->panels_ok = true;
   ctx->panels_thr = thr;
-  ctx->pt_ok = false;
   return GW_OK;
 }
 
@@ -355,10 +401,175 @@ std::vector<Batch> plan_batches(gw_ctx* ctx, size_t elem_bytes, double budget_by
       b.P1 = 0;
     }
     b.nslab = (b.s1 - b.s0) * (ctx->naop / kSlabAO);
+    b.m0 = 0;
+    b.m1 = n;
+    b.mu0 = 0;
+    b.nmu = ctx->nao;
+    b.Lc = ctx->naop;
+    b.Q0 = 0;
+    b.Q1 = ctx->nri;
     out.push_back(b);
     s = e;
   }
   return out;
+}
+
+// RI window [q0, q1) of the panels of atoms [a0, a1) (q0 = q1 = 0: none).
+void panel_window(const gw_ctx* ctx, int a0, int a1, int* q0, int* q1) {
+  int lo = INT32_MAX, hi = 0;
+  for (int a = a0; a < a1; ++a) {
+    const PanelDesc& d = ctx->panels[a];
+    if (d.K == 0) continue;
+    lo = std::min(lo, d.p0);
+    hi = std::max(hi, d.p0 + d.npw);
+  }
+  if (hi <= lo) lo = hi = 0;
+  *q0 = lo;
+  *q1 = hi;
+}
+
+// 2-D batches of the tensor-core route: chunks of mu-atoms, and in each
+// chunk batches of consecutive owner atoms under the byte budget for X and
+// Y (elem_bytes per operand element), cut where the batch's primary-function
+// count wastes the least of its last align_rows-row tile (step B runs on the
+// batch's rows in such tiles).  One chunk of every atom keeps Y over all RI
+// functions; several chunks give each its panels' RI window.
+std::vector<Batch> plan_batches_tc(gw_ctx* ctx, size_t elem_bytes, double budget_bytes, int align_rows) {
+  const int n = ctx->n_at;
+  auto seg_len = [&](int m0, int m1) {
+    const int nmu = ctx->ao_off[m1] - ctx->ao_off[m0];
+    return (nmu + kSlabAO - 1) / kSlabAO * kSlabAO;
+  };
+  int cs = ctx->mlp_mode ? n : ctx->mu_chunk_atoms;
+  if (cs <= 0 || cs > n) {
+    // fewest equal chunks for which one owner's operands stay within a
+    // budget share of 1/8 (so that batches hold several owners)
+    for (int nc = 1; nc <= n; ++nc) {
+      cs = (n + nc - 1) / nc;
+      bool ok = true;
+      for (int m0 = 0; m0 < n && ok; m0 += cs) {
+        const int m1 = std::min(n, m0 + cs);
+        int q0 = 0, q1 = ctx->nri;
+        if (nc > 1) panel_window(ctx, m0, m1, &q0, &q1);
+        const double lc = seg_len(m0, m1);
+        for (int s = 0; s < n && ok; ++s) {
+          const PanelDesc& d = ctx->panels[s];
+          if (d.K == 0) continue;
+          ok = lc * d.nsig * (double)(d.npw + (q1 - q0)) * elem_bytes <= budget_bytes / 8;
+        }
+      }
+      if (ok) break;
+    }
+  }
+  const bool single = cs >= n;
+  std::vector<Batch> out;
+  for (int m0 = 0; m0 < n; m0 += cs) {
+    const int m1 = std::min(n, m0 + cs);
+    int Q0 = 0, Q1 = ctx->nri;
+    if (!single) panel_window(ctx, m0, m1, &Q0, &Q1);
+    if (Q1 <= Q0) continue;  // no panel in the chunk: its Y is zero
+    const int Lc = seg_len(m0, m1);
+    const int qrow = Q1 - Q0;
+    int s = 0;
+    while (s < n) {
+      int e_max = s;
+      {
+        int P0 = INT32_MAX, P1 = 0;
+        long long K = 0;
+        while (e_max < n) {
+          const PanelDesc& d = ctx->panels[e_max];
+          int q0 = P0, q1 = P1;
+          if (d.K > 0) {
+            q0 = std::min(q0, d.p0);
+            q1 = std::max(q1, d.p0 + d.npw);
+          }
+          const long long K2 = K + (long long)Lc * d.nsig;
+          const double bytes = (double)K2 * ((q1 > q0 ? q1 - q0 : 0) + qrow) * elem_bytes;
+          const bool limit = ctx->batch_atoms > 0 && e_max - s >= ctx->batch_atoms;
+          if (e_max > s && (bytes > budget_bytes || limit)) break;
+          P0 = q0;
+          P1 = q1;
+          K = K2;
+          ++e_max;
+        }
+      }
+      int e_cut = e_max;
+      if (align_rows > 0 && e_max < n) {
+        double best = 2.0;
+        for (int e = e_max; e > s && e >= s + (e_max - s + 1) / 2; --e) {
+          const int R = ctx->ao_off[e] - ctx->ao_off[s];
+          const int Rp = (R + align_rows - 1) / align_rows * align_rows;
+          const double waste = (double)(Rp - R) / Rp;
+          if (waste < best - 1e-12) {
+            best = waste;
+            e_cut = e;
+          }
+        }
+      }
+      Batch b{};
+      b.s0 = s;
+      b.P0 = INT32_MAX;
+      b.P1 = 0;
+      long long K = 0;
+      for (int e = s; e < e_cut; ++e) {
+        const PanelDesc& d = ctx->panels[e];
+        if (d.K > 0) {
+          b.P0 = std::min(b.P0, d.p0);
+          b.P1 = std::max(b.P1, d.p0 + d.npw);
+        }
+        b.seg.push_back(K);
+        K += (long long)Lc * d.nsig;
+      }
+      b.s1 = e_cut;
+      b.Kb = K;
+      if (b.P1 <= b.P0) {
+        b.P0 = 0;
+        b.P1 = 0;
+      }
+      b.nslab = (b.s1 - b.s0) * (Lc / kSlabAO);
+      b.m0 = m0;
+      b.m1 = m1;
+      b.mu0 = ctx->ao_off[m0];
+      b.nmu = ctx->ao_off[m1] - ctx->ao_off[m0];
+      b.Lc = Lc;
+      b.Q0 = Q0;
+      b.Q1 = Q1;
+      out.push_back(b);
+      s = e_cut;
+    }
+  }
+  return out;
+}
+
+// Useful flops of steps A and B of one batch from the kept G blocks of this
+// tau point (flags [n_at][n_at], symmetric): step A multiplies each kept
+// block (l, s, P) of an owner s of the batch by every kept G^occ block
+// (m, l) with m in the chunk, step B each kept block (l, m, Q) of a chunk
+// atom m by every kept G^virt block (s, l) with s an owner of the batch.
+// kao[l] = sum over the chunk's atoms m of n(m) [G^occ block (m, l) kept],
+// computed once per chunk by chunk_kao.
+void chunk_kao(const gw_ctx* ctx, int m0, int m1, const std::vector<unsigned char>& fo,
+               std::vector<double>& kao) {
+  const int n = ctx->n_at;
+  kao.assign(n, 0.0);
+  for (int m = m0; m < m1; ++m)
+    for (int l = 0; l < n; ++l)
+      if (fo[(size_t)m * n + l]) kao[l] += ctx->n_ao[m];
+}
+void batch_flops_ab(const gw_ctx* ctx, const Batch& b, const std::vector<double>& kao,
+                    const std::vector<unsigned char>& fv, double* fa, double* fb) {
+  const int n = ctx->n_at;
+  std::vector<double> kav(n, 0.0);
+  for (int s = b.s0; s < b.s1; ++s)
+    for (int l = 0; l < n; ++l)
+      if (fv[(size_t)s * n + l]) kav[l] += ctx->n_ao[s];
+  double a = 0.0, v = 0.0;
+  for (int s = b.s0; s < b.s1; ++s)
+    for (int i = ctx->wl_off[s]; i < ctx->wl_off[s + 1]; ++i) a += ctx->wl_w[i] * kao[ctx->wl_atom[i]];
+  for (int m = b.m0; m < b.m1; ++m)
+    for (int i = ctx->wl_off[m]; i < ctx->wl_off[m + 1]; ++i) v += ctx->wl_w[i] * kav[ctx->wl_atom[i]];
+  *fa = a;
+  *fb = v;
 }
 
 // CUDA events bracketing the step launches of each batch (two pairs per
@@ -507,15 +718,16 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
   if ((rc = wsT(ctx, "tasks", (size_t)npt * nqt * nslab, &tasks))) return rc;
   if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
   if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
-  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, ctx->nri, ctx->d_atom_of_ri, d_len,
-                         tasks, counts, kacc, tile, per, ctx->n_at, ctx->nao, ctx->d_atom_of_ao,
+  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, 0, ctx->nri, ctx->d_atom_of_ri, d_len,
+                         tasks, counts, kacc, tile, per, 0, ctx->n_at, 0, ctx->nao, ctx->d_atom_of_ao,
                          ctx->stream);
   GW_CHECK_LAUNCH();
   double* d_fc;
   if ((rc = wsT(ctx, "fc", (size_t)ns * ctx->n_at, &d_fc))) return rc;
   int* d_nri;
   if ((rc = upload(ctx, "n_ri_b", ctx->n_ri, &d_nri))) return rc;
-  gw::launch_count_c(bx, by, ns, ctx->n_at, pa0, npa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
+  gw::launch_count_c(bx, by, ns, 0, ctx->n_at, pa0, npa, 0, ctx->n_at, d_nri, d_nao, b.s0, d_fc,
+                     ctx->stream);
   GW_CHECK_LAUNCH();
   ctx->stats.kernel_launches += 5;
 
@@ -574,15 +786,14 @@ int chi_one_batch(gw_ctx* ctx, const Batch& b, const T* g_occ, const T* g_virt, 
 // tensor-core route: transposed split panels (once per thr and slice count)
 // ---------------------------------------------------------------------------
 int ensure_pt(gw_ctx* ctx, int slices, int f16) {
-  if (ctx->pt_ok && ctx->pt_slices == slices && ctx->pt_f16 == f16 && ctx->pt_thr == ctx->panels_thr)
+  if (ctx->pt_ok && ctx->pt_slices == slices && ctx->pt_f16 == f16 && ctx->pt_thr == ctx->plan_thr)
     return GW_OK;
   free_dev(ctx->d_pt);
   ctx->d_pt = nullptr;
   ctx->pt_ok = false;
   ctx->pt_tasks.assign(ctx->n_at, gw::PanelTaskTC{});
-  std::vector<gw::PanelTaskTC> list;
   long long rows = 0;
-  int kmax = 64, max_npad = 0;
+  int kmax = 64;
   for (int s = 0; s < ctx->n_at; ++s) {
     const PanelDesc& d = ctx->panels[s];
     gw::PanelTaskTC t{};
@@ -601,27 +812,43 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
     t.lam_off = d.lam_off;
     t.ksteps = (d.K + 63) / 64;  // K steps of 64 (the tensor-core stage width)
     t.p_row0 = (int)rows;
-    const int npad = (t.N + 127) / 128 * 128;
-    rows += npad;
-    max_npad = std::max(max_npad, npad);
+    rows += (t.N + 127) / 128 * 128;
     kmax = std::max(kmax, t.ksteps * 64);
     ctx->pt_tasks[s] = t;
-    list.push_back(t);
   }
   if (rows > INT32_MAX) return fail(ctx, GW_ERR_INVALID_ARG, "transposed panels exceed 2^31 rows");
+  // rows of each kept block in the two panels it lands in: (pw of its first
+  // RI function, s' = 0)
+  const std::vector<int>& kept = ctx->plan_kept;
+  std::vector<long long> rowB(kept.size()), rowA(kept.size());
+  for (size_t i = 0; i < kept.size(); ++i) {
+    const int b = kept[i];
+    const int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
+    const gw::PanelTaskTC& tb = ctx->pt_tasks[B];
+    const gw::PanelTaskTC& ta = ctx->pt_tasks[A];
+    rowB[i] = tb.p_row0 + (long long)(ctx->ri_off[p] - tb.p0) * tb.nsig;
+    rowA[i] = ta.p_row0 + (long long)(ctx->ri_off[p] - ta.p0) * ta.nsig;
+  }
   const size_t bytes = (size_t)slices * rows * kmax * 2;
   GW_TRY(cudaMalloc(&ctx->d_pt, std::max<size_t>(bytes, 16)));
-  gw::PanelTaskTC* d_list;
+  GW_TRY(cudaMemsetAsync(ctx->d_pt, 0, std::max<size_t>(bytes, 16), ctx->stream));
   int rc;
-  if ((rc = upload(ctx, "pt_list", list, &d_list))) return rc;
+  int *d_kept, *d_kB, *d_kA, *d_nao, *d_nri;
+  long long *d_rowB, *d_rowA;
+  if ((rc = upload(ctx, "kept", kept, &d_kept)) || (rc = upload(ctx, "pt_kB", ctx->plan_kB, &d_kB)) ||
+      (rc = upload(ctx, "pt_kA", ctx->plan_kA, &d_kA)) || (rc = upload(ctx, "pt_rowB", rowB, &d_rowB)) ||
+      (rc = upload(ctx, "pt_rowA", rowA, &d_rowA)) || (rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao)) ||
+      (rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri)))
+    return rc;
   double pt_scale = 1.0;
   if (f16) {
-    // exact max |T| over the panels (viewed as rows of 1024 plus a tail)
+    // exact max |T| over the stored tensor (viewed as rows of 1024 plus a
+    // tail): a bound on every panel entry
     double *st2, h[4] = {0, 0, 0, 0};
     if ((rc = wsT(ctx, "pt_absmax", 4, &st2))) return rc;
-    const long long n = ctx->panel_elems, nrow = n / 1024;
-    gw::launch_absmax_rowsum(ctx->d_panel64, 1024, (int)nrow, 1024, st2, ctx->stream);
-    gw::launch_absmax_rowsum(ctx->d_panel64 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
+    const long long n = ctx->n_elems, nrow = n / 1024;
+    gw::launch_absmax_rowsum(ctx->d_t3, 1024, (int)nrow, 1024, st2, ctx->stream);
+    gw::launch_absmax_rowsum(ctx->d_t3 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
                              (int)(n - nrow * 1024), st2 + 2, ctx->stream);
     GW_CHECK_LAUNCH();
     GW_TRY(cudaMemcpyAsync(h, st2, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
@@ -629,8 +856,9 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
     ctx->t_absmax = std::max(h[0], h[2]);
     pt_scale = gw::pow2_scale(ctx->t_absmax);
   }
-  gw::launch_transpose_panels(ctx->d_panel64, d_list, (int)list.size(), max_npad, kmax, slices,
-                              rows * kmax, f16, pt_scale, ctx->d_pt, ctx->stream);
+  gw::launch_pt_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_kept, (long long)kept.size(),
+                        d_rowB, d_kB, d_rowA, d_kA, kmax, slices, rows * kmax, f16, pt_scale, ctx->d_pt,
+                        ctx->stream);
   GW_CHECK_LAUNCH();
   GW_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->pt_rows = rows;
@@ -638,7 +866,7 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
   ctx->pt_slices = slices;
   ctx->pt_f16 = f16;
   ctx->pt_scale = pt_scale;
-  ctx->pt_thr = ctx->panels_thr;
+  ctx->pt_thr = ctx->plan_thr;
   ctx->pt_ok = true;
   return GW_OK;
 }
@@ -701,14 +929,16 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   const double s_t = f16 ? ctx->pt_scale : 1.0;
   const int ns = b.s1 - b.s0;
   const int prow = b.P1 - b.P0;
+  const int qrow = b.Q1 - b.Q0;  // Y rows: RI functions [Q0, Q1)
+  const int nmc = b.m1 - b.m0;   // mu-atoms of the chunk
   const long long Kb = b.Kb;
-  const int n_at = ctx->n_at, nri = ctx->nri, nao = ctx->nao;
+  const int n_at = ctx->n_at, nri = ctx->nri;
   int rc;
-  if (prow == 0 || Kb == 0) return GW_OK;
+  if (prow == 0 || qrow == 0 || Kb == 0) return GW_OK;
   const int kmax = ctx->pt_kmax;
   void *xs, *ys;
   if ((rc = ws(ctx, "Xs", (size_t)slices * prow * Kb * 2, &xs))) return rc;
-  if ((rc = ws(ctx, "Ys", (size_t)slices * nri * Kb * 2, &ys))) return rc;
+  if ((rc = ws(ctx, "Ys", (size_t)slices * qrow * Kb * 2, &ys))) return rc;
   GW_TRY(cudaMemsetAsync(xs, 0, (size_t)slices * prow * Kb * 2, ctx->stream));
   if ((rc = ensure_ycover(ctx))) return rc;
   if (ctx->ycov_ok) {
@@ -717,11 +947,12 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     int* d_nao0;
     if ((rc = upload(ctx, "seg_y", b.seg, &d_seg0))) return rc;
     if ((rc = upload(ctx, "n_ao_y", ctx->n_ao, &d_nao0))) return rc;
-    gw::launch_zero_unwritten_y(ys, slices, (long long)nri * Kb, Kb, nri, ns, d_seg0, d_nao0, b.s0,
-                                ctx->d_ao_off, ctx->naop, ctx->d_ycov_lo, ctx->d_ycov_hi, ctx->stream);
+    gw::launch_zero_unwritten_y(ys, slices, (long long)qrow * Kb, Kb, b.Q0, qrow, ns, d_seg0, d_nao0,
+                                b.s0, ctx->d_ao_off, b.m0, b.m1, b.Lc, ctx->d_ycov_lo,
+                                ctx->d_ycov_hi, ctx->stream);
     GW_CHECK_LAUNCH();
   } else {
-    GW_TRY(cudaMemsetAsync(ys, 0, (size_t)slices * nri * Kb * 2, ctx->stream));
+    GW_TRY(cudaMemsetAsync(ys, 0, (size_t)slices * qrow * Kb * 2, ctx->stream));
   }
   const int pa0 = [&] {
     int a = 0;
@@ -731,11 +962,20 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   int pa1 = pa0;
   while (pa1 < n_at && ctx->ri_off[pa1] < b.P1) ++pa1;
   const int npa = pa1 - pa0;
+  // RI atoms of the Y rows
+  const int qa0 = [&] {
+    int a = 0;
+    while (ctx->ri_off[a + 1] <= b.Q0) ++a;
+    return a;
+  }();
+  int qa1 = qa0;
+  while (qa1 < n_at && ctx->ri_off[qa1] < b.Q1) ++qa1;
+  const int nqa = qa1 - qa0;
   float *bx2, *by2;
-  if ((rc = wsT(ctx, "bx2", (size_t)ns * n_at * npa, &bx2))) return rc;
-  if ((rc = wsT(ctx, "by2", (size_t)ns * n_at * n_at, &by2))) return rc;
-  GW_TRY(cudaMemsetAsync(bx2, 0, (size_t)ns * n_at * npa * sizeof(float), ctx->stream));
-  GW_TRY(cudaMemsetAsync(by2, 0, (size_t)ns * n_at * n_at * sizeof(float), ctx->stream));
+  if ((rc = wsT(ctx, "bx2", (size_t)ns * nmc * npa, &bx2))) return rc;
+  if ((rc = wsT(ctx, "by2", (size_t)ns * nmc * nqa, &by2))) return rc;
+  GW_TRY(cudaMemsetAsync(bx2, 0, (size_t)ns * nmc * npa * sizeof(float), ctx->stream));
+  GW_TRY(cudaMemsetAsync(by2, 0, (size_t)ns * nmc * nqa * sizeof(float), ctx->stream));
   int* d_err;  // zeroed once per tau point by gw_chi_tau
   if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
   CUtensorMap mp;
@@ -746,9 +986,9 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = c_event_pair(ctx, 2 * batch_idx + 1, &ea0, &ea1))) return rc;
   GW_TRY(cudaEventRecord(ea0, ctx->stream));
 
-  // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu ----
+  // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu of the chunk ----
   {
-    const int rows_a = (nao + tile - 1) / tile * tile;
+    const int rows_a = (b.nmu + tile - 1) / tile * tile;
     std::vector<gw::PanelTaskTC> ta;
     std::vector<int4> tiles;
     for (int s = b.s0; s < b.s1; ++s) {
@@ -771,33 +1011,33 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if ((rc = upload(ctx, "tc_tilesA", tiles, &d_tiles))) return rc;
       const long long g_elems = (long long)ta.size() * rows_a * kmax;
       if ((rc = ws(ctx, "GgA", (size_t)slices * g_elems * 2, &gg))) return rc;
-      gw::launch_gather_g(g_occ, nao, d_ta, (int)ta.size(), ctx->d_lam, 0, nao, rows_a, kmax, slices,
-                          g_elems, f16, s_go, gg, ctx->stream);
+      gw::launch_gather_g(g_occ, ctx->nao, d_ta, (int)ta.size(), ctx->d_lam, b.mu0, b.nmu, rows_a, kmax,
+                          slices, g_elems, f16, s_go, gg, ctx->stream);
       GW_CHECK_LAUNCH();
       CUtensorMap mg;
       if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step A)");
       if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
-                              (int)tiles.size(), d_ta, 0, nao, xs,
+                              (int)tiles.size(), d_ta, 0, b.nmu, xs,
                               (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
                               ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, npa, pa0,
-                              ctx->flush_k,
-                              d_err, ctx->stream))
+                              b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream))
         return fail(ctx, GW_ERR_CUDA, "tensor-core step A launch setup failed");
       GW_CHECK_LAUNCH();
       ctx->stats.kernel_launches += 2;
     }
   }
-  // ---- step B: Y[Q][(s, mu, s')] for every panel, rows sigma of the batch ----
+  // ---- step B: Y[Q][(s, mu, s')] for the panels of the chunk, rows sigma of the batch ----
   {
     const int r0 = ctx->ao_off[b.s0];
     const int R = ctx->ao_off[b.s1] - r0;
     const int rows_b = (R + tile - 1) / tile * tile;
     std::vector<gw::PanelTaskTC> tb;
     std::vector<int4> tiles;
-    for (int m = 0; m < n_at; ++m) {
+    for (int m = b.m0; m < b.m1; ++m) {
       gw::PanelTaskTC t = ctx->pt_tasks[m];
       if (t.K == 0) continue;
+      t.aom -= b.mu0;  // chunk-local first AO of the panel's owner
       t.g_row0 = (int)tb.size() * rows_b;
       const int ntn = (t.N + tile - 1) / tile;
       for (int nt = 0; nt < ntn; ++nt)
@@ -826,7 +1066,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if ((rc = upload(ctx, "rowsl", rowsl, &d_rowsl))) return rc;
       const long long g_elems = (long long)tb.size() * rows_b * kmax;
       if ((rc = ws(ctx, "GgB", (size_t)slices * g_elems * 2, &gg))) return rc;
-      gw::launch_gather_g(g_virt, nao, d_tb, (int)tb.size(), ctx->d_lam, r0, R, rows_b, kmax, slices,
+      gw::launch_gather_g(g_virt, ctx->nao, d_tb, (int)tb.size(), ctx->d_lam, r0, R, rows_b, kmax, slices,
                           g_elems, f16, s_gv, gg, ctx->stream);
       GW_CHECK_LAUNCH();
       CUtensorMap mg;
@@ -834,46 +1074,45 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
       if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
                               (int)tiles.size(), d_tb, 1, R, ys,
-                              (long long)nri * Kb, Kb, 0, d_rowbase, d_rowmul, d_rowsl, by2,
-                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, n_at, 0,
-                              ctx->flush_k,
-                              d_err, ctx->stream))
+                              (long long)qrow * Kb, Kb, b.Q0, d_rowbase, d_rowmul, d_rowsl, by2,
+                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, nqa, qa0,
+                              b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream))
         return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
       GW_CHECK_LAUNCH();
       ctx->stats.kernel_launches += 2;
     }
   }
   GW_TRY(cudaEventRecord(ea1, ctx->stream));
-  ctx->stats.bytes_operands += (double)(prow + nri) * Kb * 2.0 * slices;
+  ctx->stats.bytes_operands += (double)(prow + qrow) * Kb * 2.0 * slices;
 
   // ---- block filter, occupancy, task lists ----
   const int nslab = b.nslab;
-  const int npt = (prow + tile - 1) / tile, nqt = (nri + tile - 1) / tile;
+  const int npt = (prow + tile - 1) / tile, nqt = (qrow + tile - 1) / tile;
   unsigned char *bx, *by, *fx, *fy;
-  if ((rc = wsT(ctx, "bx", (size_t)ns * n_at * npa, &bx))) return rc;
-  if ((rc = wsT(ctx, "by", (size_t)ns * n_at * n_at, &by))) return rc;
-  if ((rc = wsT(ctx, "fx", (size_t)ns * ctx->n_at * npt, &fx))) return rc;
-  if ((rc = wsT(ctx, "fy", (size_t)ns * ctx->n_at * nqt, &fy))) return rc;
-  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)ns * ctx->n_at * npt, ctx->stream));
-  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)ns * ctx->n_at * nqt, ctx->stream));
+  if ((rc = wsT(ctx, "bx", (size_t)ns * nmc * npa, &bx))) return rc;
+  if ((rc = wsT(ctx, "by", (size_t)ns * nmc * nqa, &by))) return rc;
+  if ((rc = wsT(ctx, "fx", (size_t)ns * nmc * npt, &fx))) return rc;
+  if ((rc = wsT(ctx, "fy", (size_t)ns * nmc * nqt, &fy))) return rc;
+  GW_TRY(cudaMemsetAsync(fx, 0, (size_t)ns * nmc * npt, ctx->stream));
+  GW_TRY(cudaMemsetAsync(fy, 0, (size_t)ns * nmc * nqt, ctx->stream));
   long long* d_seg;
   int* d_nao;
   if ((rc = upload(ctx, "seg", b.seg, &d_seg))) return rc;
   if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao))) return rc;
   // queue of filtered blocks to zero (shared by the two stream-ordered calls)
   int *zlist, *zcount;
-  if ((rc = wsT(ctx, "zlist", (size_t)ns * n_at * n_at, &zlist))) return rc;
+  if ((rc = wsT(ctx, "zlist", (size_t)ns * nmc * std::max(npa, nqa), &zlist))) return rc;
   if ((rc = wsT(ctx, "zcount", 1, &zcount))) return rc;
   gw::launch_slices_block_filter(xs, slices, (long long)prow * Kb, Kb, b.P0, ctx->d_ri_off,
-                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, pa0, npa, n_at, thr, bx2, bx,
-                                 fx, npt, tile, zlist, zcount, ctx->stream);
-  gw::launch_slices_block_filter(ys, slices, (long long)nri * Kb, Kb, 0, ctx->d_ri_off, ctx->d_ao_off,
-                                 d_nao, b.s0, ns, d_seg, 0, n_at, n_at, thr, by2, by, fy, nqt, tile,
-                                 zlist, zcount, ctx->stream);
+                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, pa0, npa, b.m0, nmc, b.mu0, thr,
+                                 bx2, bx, fx, npt, tile, zlist, zcount, ctx->stream);
+  gw::launch_slices_block_filter(ys, slices, (long long)qrow * Kb, Kb, b.Q0, ctx->d_ri_off,
+                                 ctx->d_ao_off, d_nao, b.s0, ns, d_seg, qa0, nqa, b.m0, nmc, b.mu0, thr,
+                                 by2, by, fy, nqt, tile, zlist, zcount, ctx->stream);
   GW_CHECK_LAUNCH();
   std::vector<long long> slab_k0(nslab);
   std::vector<int> slab_len(nslab);
-  const int per = ctx->naop / kSlabAO;
+  const int per = b.Lc / kSlabAO;
   for (int sl = 0; sl < ns; ++sl)
     for (int c = 0; c < per; ++c) {
       const int nsig = ctx->n_ao[b.s0 + sl];
@@ -889,13 +1128,14 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = wsT(ctx, "tasks", (size_t)npt * nqt * nslab, &tasks))) return rc;
   if ((rc = wsT(ctx, "counts", (size_t)npt * nqt, &counts))) return rc;
   if ((rc = wsT(ctx, "kacc", (size_t)npt * nqt, &kacc))) return rc;
-  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
-                         counts, kacc, tile, per, n_at, nao, ctx->d_atom_of_ao, ctx->stream);
+  gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, b.Q0, qrow, ctx->d_atom_of_ri, d_len,
+                         tasks, counts, kacc, tile, per, b.m0, nmc, b.mu0, b.nmu, ctx->d_atom_of_ao,
+                         ctx->stream);
   double* d_fc;
   int* d_nri;
-  if ((rc = wsT(ctx, "fc", (size_t)ns * n_at, &d_fc))) return rc;
+  if ((rc = wsT(ctx, "fc", (size_t)ns * nmc, &d_fc))) return rc;
   if ((rc = upload(ctx, "n_ri_b", ctx->n_ri, &d_nri))) return rc;
-  gw::launch_count_c(bx, by, ns, n_at, pa0, npa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
+  gw::launch_count_c(bx, by, ns, b.m0, nmc, pa0, npa, qa0, nqa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
   GW_CHECK_LAUNCH();
   ctx->stats.kernel_launches += 4;
   double fc_scale = 1.0;
@@ -940,7 +1180,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   }
   CUtensorMap mx, my;
   if (gw::make_slice_map(&mx, xs, Kb, prow, slices, tile, f16) ||
-      gw::make_slice_map(&my, ys, Kb, nri, slices, tile, f16))
+      gw::make_slice_map(&my, ys, Kb, qrow, slices, tile, f16))
     return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the step-C operands");
   cudaEvent_t ec0, ec1;
   if ((rc = c_event_pair(ctx, 2 * batch_idx, &ec0, &ec1))) return rc;
@@ -971,8 +1211,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, w.u_tile, w.u_first,
                                 w.u_count, (int)std::min<size_t>(cap, INT32_MAX), w.n_units, tasks,
-                                counts, nslab, d_k0, d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k,
-                                d_err, ctx->stream))
+                                counts, nslab, d_k0, d_len, b.P0, prow, nri, b.Q0, qrow, nqt, acc,
+                                ctx->flush_k, d_err, ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
     GW_CHECK_LAUNCH();
     GW_TRY(cudaEventRecord(ec1, ctx->stream));
@@ -980,10 +1220,10 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     ctx->stats.kernel_launches += 1;
     double* d_fc_all;
     if ((rc = wsT(ctx, "fc_all", (size_t)n_at * n_at, &d_fc_all))) return rc;
-    GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * n_at * sizeof(double),
+    GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * nmc * sizeof(double),
                            cudaMemcpyDeviceToDevice, ctx->stream));
-    ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * n_at, fc_scale_dev});
-    ctx->tc_fc_used += (long long)ns * n_at;
+    ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * nmc, fc_scale_dev});
+    ctx->tc_fc_used += (long long)ns * nmc;
     ctx->stats.tiles_total += (long long)ntiles;
     ctx->stats.slabs_total += (long long)ntiles * nslab;
     ctx->stats.flops_issued += issued;
@@ -1066,8 +1306,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_ut, d_uf, d_uc,
                                 (int)u_tile.size(), nullptr, tasks, counts,
-                                nslab, d_k0, d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err,
-                                ctx->stream))
+                                nslab, d_k0, d_len, b.P0, prow, nri, b.Q0, qrow, nqt, acc, ctx->flush_k,
+                                d_err, ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
   } else {
     int* d_active;
@@ -1075,7 +1315,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_active,
                           (int)active.size(), tasks, counts, nslab, d_k0,
-                          d_len, b.P0, prow, nri, nqt, acc, ctx->flush_k, d_err, ctx->stream))
+                          d_len, b.P0, prow, nri, b.Q0, qrow, nqt, acc, ctx->flush_k, d_err,
+                          ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
   }
   GW_CHECK_LAUNCH();
@@ -1086,10 +1327,10 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   // the tau point (tc_finish_tau), so the next batch is queued without a wait
   double* d_fc_all;  // sized n_at * n_at by gw_chi_tau
   if ((rc = wsT(ctx, "fc_all", (size_t)n_at * n_at, &d_fc_all))) return rc;
-  GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * n_at * sizeof(double),
+  GW_TRY(cudaMemcpyAsync(d_fc_all + ctx->tc_fc_used, d_fc, (size_t)ns * nmc * sizeof(double),
                          cudaMemcpyDeviceToDevice, ctx->stream));
-  ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * n_at, fc_scale});
-  ctx->tc_fc_used += (long long)ns * n_at;
+  ctx->tc_pending.push_back({batch_idx, ctx->tc_fc_used, ns * nmc, fc_scale});
+  ctx->tc_fc_used += (long long)ns * nmc;
   long long act = 0, sl_act = 0;
   double ksum = 0.0;
   for (size_t t = 0; t < h_counts.size(); ++t) {
@@ -1419,6 +1660,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->flush_k = (int)value;
     return GW_OK;
   }
+  if (!strcmp(key, "mu_chunk_atoms")) {
+    if (!(value >= 0 && value <= 1e9)) return fail(ctx, GW_ERR_INVALID_ARG, "mu_chunk_atoms must be >= 0");
+    ctx->mu_chunk_atoms = (int)value;
+    return GW_OK;
+  }
   if (!strcmp(key, "batch_atoms")) {
     if (!(value >= 0)) return fail(ctx, GW_ERR_INVALID_ARG, "batch_atoms must be >= 0");
     ctx->batch_atoms = (int)value;
@@ -1497,7 +1743,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     ~StallScope() { gw::tc_set_stall_test(0); }
   } stall_scope(ctx->test_stall);
   int rc;
-  if ((rc = build_panels(ctx, thr))) return rc;
+  // the tensor-core route needs the panel plan only; the CUDA-core routes
+  // also the FP64 panel pool
+  if ((rc = tc_prec ? plan_panels(ctx, thr) : build_panels(ctx, thr))) return rc;
   const bool f64 = precision == GW_FP64;
   const bool tcpath = tc_prec;
   const int f16 = precision == GW_FP16X3;
@@ -1512,7 +1760,8 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   const size_t esz = f64 ? sizeof(double)
                          : precision == GW_BF16X6 ? 6 : tcpath ? 4 : sizeof(float);
   std::vector<Batch> batches =
-      plan_batches(ctx, esz, ctx->batch_bytes, tcpath ? gw::tc_tile_rows() : 0);
+      tcpath ? plan_batches_tc(ctx, esz, ctx->batch_bytes, gw::tc_tile_rows())
+             : plan_batches(ctx, esz, ctx->batch_bytes, 0);
   ctx->stats.n_batches = (int)batches.size();
 
   double *cso, *csv, *go, *gv, *acc, *stage = nullptr;
@@ -1530,10 +1779,6 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     if ((rc = wsT(ctx, "g_occ32", (size_t)nao * nao, &go32))) return rc;
     if ((rc = wsT(ctx, "g_virt32", (size_t)nao * nao, &gv32))) return rc;
   }
-  // per-block useful-flop weights of steps A and B: 2 nA nB nP, both orientations
-  std::vector<int> kept_blocks;
-  for (long long b = 0; b < ctx->n_blocks; ++b)
-    if (!(ctx->blk_norm[b] < thr)) kept_blocks.push_back((int)b);
 
   gw::ScopedEvents<3> ev;
   GW_TRY(ev.create());
@@ -1571,6 +1816,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
       ctx->stats.kernel_launches += 2;
       GW_TRY(cudaMemcpyAsync(hfo.data(), flo, hfo.size(), cudaMemcpyDeviceToHost, ctx->stream));
       GW_TRY(cudaMemcpyAsync(hfv.data(), flv, hfv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      GW_TRY(cudaStreamSynchronize(ctx->stream));  // the batch plan below reads the flags
     }
     if (!f64 && !tcpath) {
       gw::launch_cast_f64_f32(go, go32, (long long)nao * nao, ctx->stream);
@@ -1582,8 +1828,25 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     GW_TRY(cudaEventRecord(ev[1], ctx->stream));
     std::vector<double> fc;
     if (tcpath && (rc = tc_begin_tau(ctx))) return rc;
+    double fa = 0.0, fb = 0.0;
+    std::vector<double> kao;
+    int kao_m0 = -1;
     for (size_t bi = 0; bi < batches.size(); ++bi) {
       const Batch& b = batches[bi];
+      // useful flops of steps A and B; a batch whose X or Y is all zero
+      // (every G block it needs was filtered) adds nothing to chi: skipped
+      if (b.m0 != kao_m0) {
+        chunk_kao(ctx, b.m0, b.m1, hfo, kao);
+        kao_m0 = b.m0;
+      }
+      double ba = 0.0, bb = 0.0;
+      batch_flops_ab(ctx, b, kao, hfv, &ba, &bb);
+      if (ba == 0.0 || bb == 0.0) {
+        ++ctx->stats.batches_skipped;
+        continue;
+      }
+      fa += ba;
+      fb += bb;
       if (f64)
         rc = chi_one_batch<double>(ctx, b, go, gv, ctx->d_panel64, thr, acc, fc, precision, bi);
       else if (tcpath)
@@ -1607,24 +1870,6 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     GW_TRY(cudaEventElapsedTime(&t12, ev[1], ev[2]));
     ms_g += t01;
     ms_c += t12;
-    // useful flops of steps A and B for this tau
-    std::vector<double> kao_o(n_at, 0.0), kao_v(n_at, 0.0);
-    for (int l = 0; l < n_at; ++l)
-      for (int m = 0; m < n_at; ++m) {
-        if (hfo[(size_t)m * n_at + l]) kao_o[l] += ctx->n_ao[m];
-        if (hfv[(size_t)m * n_at + l]) kao_v[l] += ctx->n_ao[m];
-      }
-    double fa = 0.0, fb = 0.0;
-    for (int b : kept_blocks) {
-      int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1], P = ctx->blk[3 * b + 2];
-      double w = 2.0 * ctx->n_ao[A] * ctx->n_ao[B] * ctx->n_ri[P];
-      fa += w * kao_o[A];
-      fb += w * kao_v[A];
-      if (A != B) {
-        fa += w * kao_o[B];
-        fb += w * kao_v[B];
-      }
-    }
     double fcs = 0.0;
     for (double v : fc) fcs += v;
     ctx->stats.flops_a += fa;

@@ -80,12 +80,20 @@ struct PanelTaskTC {
   int s_local, owner, lam_off;
 };
 
+// One operand batch: the sigma-atoms (owners) [s0, s1) against the chunk of
+// mu-atoms [m0, m1).  K runs over (owner s, chunk-local mu < Lc, sigma' of s);
+// X rows are the RI window [P0, P1) of the owners' panels, Y rows the RI
+// window [Q0, Q1) of the chunk's panels.  A chunk of every atom has Lc =
+// n_AO rounded to kSlabAO and Y over all RI functions.
 struct Batch {
   int s0, s1;         // owner atoms [s0, s1)
   int P0, P1;         // RI window of X rows
-  long long Kb;       // K length (sum over owners of naop * nsig)
-  int nslab;          // (s1 - s0) * naop / kSlabAO
+  long long Kb;       // K length (sum over owners of Lc * nsig)
+  int nslab;          // (s1 - s0) * Lc / kSlabAO
   std::vector<long long> seg;  // per owner: K offset
+  int m0 = 0, m1 = 0;          // mu-atom chunk
+  int mu0 = 0, nmu = 0, Lc = 0;  // its AOs [mu0, mu0 + nmu), K segment length per sigma'
+  int Q0 = 0, Q1 = 0;          // RI window of Y rows
 };
 
 // Builds (or reuses) the owner panels of the 3c tensor for filter threshold
@@ -153,10 +161,23 @@ struct gw_ctx {
   double mu = 0.0;
   std::vector<double> tau;
 
-  // panels (depend on thr through the 3c block filter)
+  // panel plan (depends on thr through the 3c block filter): descriptors,
+  // the kept blocks with the K offset of their partner atom in each owner's
+  // panel, and the device lambda lists; every route needs it
+  bool plan_ok = false;
+  double plan_thr = -1.0;
+  std::vector<gw::PanelDesc> panels;   // per atom (K == 0: no panel)
+  std::vector<int> plan_kept;          // kept 3c blocks
+  std::vector<int> plan_kB, plan_kA;   // per kept block (A, B, P): K offset of A in panel(B), of B in panel(A)
+  // per owner s: (lambda-atom l, sum over its kept blocks (l, s, P) of
+  // 2 n(l) n(s) n(P)), CSR; the useful flops of steps A and B per batch
+  std::vector<int> wl_off, wl_atom;
+  std::vector<double> wl_w;
+  // FP64 panel pool (CUDA-core routes, the self-energy and the allocation-free
+  // entry point; the tensor-core route builds its split panels from the
+  // stored blocks instead)
   bool panels_ok = false;
   double panels_thr = -1.0;
-  std::vector<gw::PanelDesc> panels;   // per atom (K == 0: no panel)
   long long panel_elems = 0;
   double* d_panel64 = nullptr;
   float* d_panel32 = nullptr;
@@ -217,6 +238,9 @@ struct gw_ctx {
   // step-C work units: tiles split into runs of about c_split_k reduction
   // elements, FP64 atomics into chi (0: whole tiles, bitwise reproducible)
   int c_split_k = 2048;
+  // mu-atoms per chunk of the tensor-core route's 2-D batches (0: the fewest
+  // equal chunks that keep one owner's operands within budget / 8)
+  int mu_chunk_atoms = 0;
 
   // named device work buffers (grown on demand) and the step timing events
   // of this context; a context is used by one host thread at a time

@@ -30,8 +30,9 @@
 //    first call before any stream capture begins.
 //  * Each call copies its per-batch tables from pageable host memory and
 //    synchronises the context's stream after every batch and at its end.
-//  * The 3c tensor panels are built by gw_chi_tau (they depend on thr); call
-//    gw_chi_tau once with the same thr before using this entry point.
+//  * The FP64 3c tensor panels are built by gw_chi_tau on its CUDA-core
+//    routes (they depend on thr); call gw_chi_tau once with the same thr and
+//    precision GW_FP64 (or GW_FP32) before using this entry point.
 //  * No cudaMalloc, cudaFree or allocating library routine is called.
 #include <cuda_runtime.h>
 
@@ -137,8 +138,8 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
   }
   if (!ctx->panels_ok || ctx->panels_thr != thr) {
     ctx->err =
-        "gw_chi_tau_noalloc: the 3c panels for this thr are not built; call gw_chi_tau once "
-        "with the same thr first";
+        "gw_chi_tau_noalloc: the FP64 3c panels for this thr are not built; call gw_chi_tau "
+        "once with the same thr and precision GW_FP64 (or GW_FP32) first";
     return GW_ERR_ORDER;
   }
   NA_TRY(cudaSetDevice(ctx->device));
@@ -356,8 +357,8 @@ extern "C" int gw_chi_tau_noalloc(gw_ctx* ctx, int tau_index, double thr, double
     gw::launch_operand_block_filter<double>(Y, Kb, 0, ctx->d_ri_off, ctx->d_ao_off, d_nao, b.s0, ns,
                                             d_seg, 0, n_at, n_at, thr, naop, by, fy, nqt, 64, st);
     NA_LAUNCHED();
-    gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, nri, ctx->d_atom_of_ri, d_len, tasks,
-                           counts, kacc, 64, per, n_at, nao, ctx->d_atom_of_ao, st);
+    gw::launch_build_tasks(fx, fy, nslab, npt, nqt, b.P0, prow, 0, nri, ctx->d_atom_of_ri, d_len, tasks,
+                           counts, kacc, 64, per, 0, n_at, 0, nao, ctx->d_atom_of_ao, st);
     gw::launch_chi_tiles<double, double>(X, Y, Kb, b.P0, prow, nri, tasks, counts, nslab, npt, nqt,
                                          d_k0, d_len, acc, st);
     NA_LAUNCHED();

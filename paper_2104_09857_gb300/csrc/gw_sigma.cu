@@ -285,7 +285,8 @@ int sigma_impl(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orb
         if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_b * s_w)), m_b, m_w, (const int*)b_tl1.p,
                               n_tiles1, (const int*)b_tk1.p,
                               (const int*)b_ct1.p, nslab, (const long long*)b_k01.p,
-                              (const int*)b_ln1.p, 0, nao, nri, nqt1, y, ctx->flush_k, (int*)b_err.p, st)) {
+                              (const int*)b_ln1.p, 0, nao, nri, 0, nri, nqt1, y, ctx->flush_k,
+                              (int*)b_err.p, st)) {
           ctx->err = "gw_sigma_tau: tensor-core launch setup failed";
           return GW_ERR_CUDA;
         }
@@ -295,7 +296,8 @@ int sigma_impl(gw_ctx* ctx, const double* W_tau, int w_on_device, const int* orb
         if (gw::launch_chi_tc(slices, f16, (float)(1.0 / (s_y * s_b)), m_y, m_bq, (const int*)b_tl2.p,
                               n_tiles2, (const int*)b_tk2.p,
                               (const int*)b_ct2.p, nslab, (const long long*)b_k01.p,
-                              (const int*)b_ln1.p, 0, nao, nao, nqt2, z, ctx->flush_k, (int*)b_err.p, st)) {
+                              (const int*)b_ln1.p, 0, nao, nao, 0, nao, nqt2, z, ctx->flush_k,
+                              (int*)b_err.p, st)) {
           ctx->err = "gw_sigma_tau: tensor-core launch setup failed";
           return GW_ERR_CUDA;
         }

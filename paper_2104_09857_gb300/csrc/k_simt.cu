@@ -394,15 +394,15 @@ __global__ void k_operand_block_filter(T* __restrict__ Z, long long ldk, int row
 // whose Y part touches the Q tile.  Tiles entirely below the atom-block
 // diagonal (atom(first P) > atom(last Q)) get no tasks.
 __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsigned char* __restrict__ fy,
-                              int nslab, int npt, int nqt, int P0, int prow, int nri,
+                              int nslab, int npt, int nqt, int P0, int prow, int Q0, int qrow,
                               const int* __restrict__ atom_of_ri, const int* __restrict__ slab_len,
                               int* __restrict__ tasks, int* __restrict__ counts,
-                              long long* __restrict__ kacc, int tile_rows, int per, int n_at, int nao,
-                              const int* __restrict__ atom_of_ao) {
+                              long long* __restrict__ kacc, int tile_rows, int per, int m0, int nmc,
+                              int mu0, int nmu, const int* __restrict__ atom_of_ao) {
   int tile = blockIdx.x;
   int pt = tile / nqt, qt = tile % nqt;
   int pfirst = P0 + pt * tile_rows;
-  int qlast = min(nri, (qt + 1) * tile_rows) - 1;
+  int qlast = Q0 + min(qrow, (qt + 1) * tile_rows) - 1;
   bool upper = atom_of_ri[pfirst] <= atom_of_ri[qlast];
   // warp-serial compaction in slab order (deterministic)
   if (threadIdx.x >= 32) return;
@@ -418,11 +418,12 @@ __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsign
         // row tile and a Y block in the column tile (otherwise the product is
         // exactly zero)
         const int sl = s / per, c = s % per;
-        const int a_lo = c * kSlabAO;
-        if (a_lo < nao) {
-          const int m0 = atom_of_ao[a_lo], m1 = atom_of_ao[min(nao, a_lo + kSlabAO) - 1];
-          for (int m = m0; m <= m1 && !on; ++m)
-            on = fx[((long long)sl * n_at + m) * npt + pt] && fy[((long long)sl * n_at + m) * nqt + qt];
+        const int a_lo = c * kSlabAO;  // chunk-local AO
+        if (a_lo < nmu) {
+          const int ma = atom_of_ao[mu0 + a_lo] - m0;
+          const int mb = atom_of_ao[mu0 + min(nmu, a_lo + kSlabAO) - 1] - m0;
+          for (int m = ma; m <= mb && !on; ++m)
+            on = fx[((long long)sl * nmc + m) * npt + pt] && fy[((long long)sl * nmc + m) * nqt + qt];
         }
       }
       unsigned m = __ballot_sync(0xffffffffu, on);
@@ -441,28 +442,31 @@ __global__ void k_build_tasks(const unsigned char* __restrict__ fx, const unsign
   (void)prow;
 }
 
-// Useful flops of step C for one batch: for each (s, m) pair,
-//   sum_{p <= q} 2 n(m) n(s) nP nQ [X(m,s,p) kept][Y(m,s,q) kept].
+// Useful flops of step C for one batch: for each (s, m) pair of the batch's
+// sigma-atoms and the chunk's mu-atoms,
+//   sum_{p <= q} 2 n(m) n(s) nP nQ [X(m,s,p) kept][Y(m,s,q) kept],
+// X flags over RI atoms [pa0, pa0 + npa), Y flags over [qa0, qa0 + nqa).
 __global__ void k_count_c(const unsigned char* __restrict__ bx, const unsigned char* __restrict__ by,
-                          int ns, int n_at, int pa0, int npa, const int* __restrict__ n_ri,
-                          const int* __restrict__ n_ao, int s0, double* __restrict__ out) {
+                          int ns, int m0, int nmc, int pa0, int npa, int qa0, int nqa,
+                          const int* __restrict__ n_ri, const int* __restrict__ n_ao, int s0,
+                          double* __restrict__ out) {
   int pair = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pair >= ns * n_at) return;
-  int sl = pair / n_at, m = pair % n_at;
-  const unsigned char* fx = bx + ((long long)sl * n_at + m) * npa;
-  const unsigned char* fy = by + ((long long)sl * n_at + m) * n_at;
+  if (pair >= ns * nmc) return;
+  int sl = pair / nmc, ml = pair % nmc;
+  const unsigned char* fx = bx + ((long long)sl * nmc + ml) * npa;
+  const unsigned char* fy = by + ((long long)sl * nmc + ml) * nqa;
   // suffix sums of Y over q
   double tot = 0.0, suffix = 0.0;
-  int q = n_at - 1;
+  int q = qa0 + nqa - 1;
   for (int pl = npa - 1; pl >= 0; --pl) {
     int p = pa0 + pl;
-    while (q >= p) {
-      if (fy[q]) suffix += n_ri[q];
+    while (q >= p && q >= qa0) {
+      if (fy[q - qa0]) suffix += n_ri[q];
       --q;
     }
     if (fx[pl]) tot += (double)n_ri[p] * suffix;
   }
-  out[pair] = 2.0 * tot * n_ao[m] * n_ao[s0 + sl];
+  out[pair] = 2.0 * tot * n_ao[m0 + ml] * n_ao[s0 + sl];
 }
 
 // chi_out[P][Q] = acc[P][Q] if atom(P) <= atom(Q) else acc[Q][P]
@@ -557,19 +561,23 @@ template void launch_operand_block_filter<float>(float*, long long, int, const i
                                                  int, int, cudaStream_t);
 
 void launch_build_tasks(const unsigned char* fx, const unsigned char* fy, int nslab, int npt,
-                        int nqt, int P0, int prow, int nri, const int* atom_of_ri,
+                        int nqt, int P0, int prow, int Q0, int qrow, const int* atom_of_ri,
                         const int* slab_len, int* tasks, int* counts, long long* kacc,
-                        int tile_rows, int per, int n_at, int nao, const int* atom_of_ao,
-                        cudaStream_t st) {
-  k_build_tasks<<<npt * nqt, 32, 0, st>>>(fx, fy, nslab, npt, nqt, P0, prow, nri, atom_of_ri,
-                                          slab_len, tasks, counts, kacc, tile_rows, per, n_at, nao,
-                                          atom_of_ao);
+                        int tile_rows, int per, int m0, int nmc, int mu0, int nmu,
+                        const int* atom_of_ao, cudaStream_t st) {
+  if (npt * nqt == 0) return;
+  k_build_tasks<<<npt * nqt, 32, 0, st>>>(fx, fy, nslab, npt, nqt, P0, prow, Q0, qrow, atom_of_ri,
+                                          slab_len, tasks, counts, kacc, tile_rows, per, m0, nmc, mu0,
+                                          nmu, atom_of_ao);
 }
 
-void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int n_at, int pa0,
-                    int npa, const int* n_ri, const int* n_ao, int s0, double* out, cudaStream_t st) {
-  int n = ns * n_at;
-  k_count_c<<<(n + 127) / 128, 128, 0, st>>>(bx, by, ns, n_at, pa0, npa, n_ri, n_ao, s0, out);
+void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int m0, int nmc, int pa0,
+                    int npa, int qa0, int nqa, const int* n_ri, const int* n_ao, int s0, double* out,
+                    cudaStream_t st) {
+  int n = ns * nmc;
+  if (n == 0) return;
+  k_count_c<<<(n + 127) / 128, 128, 0, st>>>(bx, by, ns, m0, nmc, pa0, npa, qa0, nqa, n_ri, n_ao, s0,
+                                             out);
 }
 
 template <typename T, typename AccT>

@@ -29,15 +29,18 @@ void launch_operand_block_filter(T* Z, long long ldk, int rowoff, const int* ri_
                                  const long long* seg, int pa0, int npa, int n_at, double thr,
                                  int naop, unsigned char* blockflag, unsigned char* tileflag,
                                  int ntile, int tile_rows, cudaStream_t st);
-// Occupancy flags are per (sigma-atom of the batch, mu-atom, tile):
-// fx[(sl * n_at + m) * npt + pt], fy[(sl * n_at + m) * nqt + qt].
+// Occupancy flags are per (sigma-atom of the batch, mu-atom of the chunk,
+// tile): fx[(sl * nmc + m - m0) * npt + pt], fy[(sl * nmc + m - m0) * nqt + qt].
+// The chunk's AOs are [mu0, mu0 + nmu); slabs are 64 chunk-local AOs (per
+// slabs per sigma-atom); the Y rows are RI functions [Q0, Q0 + qrow).
 void launch_build_tasks(const unsigned char* fx, const unsigned char* fy, int nslab, int npt,
-                        int nqt, int P0, int prow, int nri, const int* atom_of_ri,
+                        int nqt, int P0, int prow, int Q0, int qrow, const int* atom_of_ri,
                         const int* slab_len, int* tasks, int* counts, long long* kacc,
-                        int tile_rows, int per, int n_at, int nao, const int* atom_of_ao,
-                        cudaStream_t st);
-void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int n_at, int pa0,
-                    int npa, const int* n_ri, const int* n_ao, int s0, double* out, cudaStream_t st);
+                        int tile_rows, int per, int m0, int nmc, int mu0, int nmu,
+                        const int* atom_of_ao, cudaStream_t st);
+void launch_count_c(const unsigned char* bx, const unsigned char* by, int ns, int m0, int nmc, int pa0,
+                    int npa, int qa0, int nqa, const int* n_ri, const int* n_ao, int s0, double* out,
+                    cudaStream_t st);
 template <typename T, typename AccT>
 void launch_chi_tiles(const T* X, const T* Y, long long ldk, int P0, int prow, int nri,
                       const int* tasks, const int* counts, int max_slab, int npt, int nqt,

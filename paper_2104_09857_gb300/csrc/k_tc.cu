@@ -255,6 +255,7 @@ struct ChiJob {
   const long long* slab_k0;
   const int* slab_len;
   int nqt, P0, prow, nri;
+  int Q0, qrow;     // Y rows are RI functions [Q0, Q0 + qrow)
   double* chi;
   float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
   const int* n_dev; // optional: number of units in device memory (n_tiles = capacity)
@@ -327,13 +328,14 @@ struct ChiJob {
       for (int j = 0; j < kStgCols; ++j) f[lane * kStgPitch + j] = acc[cc + j];
       __syncwarp();
       const int col = lane % kStgCols, sub = lane / kStgCols;
-      const int q = T.yb + c0 + cc + col;
+      const int ql = T.yb + c0 + cc + col;  // Y row
+      const int q = Q0 + ql;
       if (unit_first) {
         // units of one tile may run concurrently when K is split
 #pragma unroll
         for (int i = 0; i < 32; i += kRowsPer) {
           const int p = T.ya + quad * 32 + i + sub;
-          if (p < prow && q < nri)
+          if (p < prow && ql < qrow)
             atomicAdd(chi + static_cast<long long>(P0 + p) * nri + q,
                       -static_cast<double>(f[(i + sub) * kStgPitch + col] * out_scale));
         }
@@ -343,12 +345,12 @@ struct ChiJob {
 #pragma unroll
         for (int i = 0; i < 32 / kRowsPer; ++i) {
           const int p = T.ya + quad * 32 + kRowsPer * i + sub;
-          old[i] = (p < prow && q < nri) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
+          old[i] = (p < prow && ql < qrow) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
         }
 #pragma unroll
         for (int i = 0; i < 32 / kRowsPer; ++i) {
           const int p = T.ya + quad * 32 + kRowsPer * i + sub;
-          if (p < prow && q < nri)
+          if (p < prow && ql < qrow)
             chi[static_cast<long long>(P0 + p) * nri + q] =
                 old[i] - static_cast<double>(f[(kRowsPer * i + sub) * kStgPitch + col] * out_scale);
         }
@@ -394,11 +396,12 @@ struct PanelJob {
   const long long* rowbase;   // mode 1, per batch row
   const int* rowmul;
   const int* row_slocal;
-  float* norm2;               // mode 0: [ns][n_at][npa], mode 1: [ns][n_at][n_at]
+  float* norm2;               // [ns][nmc][npa]: sigma-atom of the batch, mu-atom of the chunk, RI atom
   const int* atom_of_ri;
   const int* atom_of_ao;
   const int* ao_off;
   int n_at, npa, pa0, slices;
+  int mu_base, m_base, nmc;   // mu chunk: first AO, first atom, atom count
   int f16;                    // slices in binary16 (else bf16)
   float unscale;              // 1 / (scale of Gg x scale of PT): true Z = acc * unscale
   float out_scale;            // scale of the Z slices
@@ -451,10 +454,10 @@ struct PanelJob {
       const int sp = n - pw * tk.nsig;
       const int patom = n_ok ? atom_of_ri[tk.p0 + pw] : 0;
       uint16_t* o = out + static_cast<long long>(tk.p0 + pw - P0b) * ldk + tk.seg + sp;
-      const int mu0 = T.nt * kTileN + c0;
-      const int base_key = n_ok ? tk.s_local * n_at * npa + (patom - pa0) : -1;
-      int m = atom_of_ao[mu0 < rows_valid ? mu0 : rows_valid - 1];
-      int mend = ao_off[m + 1];
+      const int mu0 = T.nt * kTileN + c0;  // chunk-local
+      const int base_key = n_ok ? tk.s_local * nmc * npa + (patom - pa0) : -1;
+      int m = atom_of_ao[mu_base + (mu0 < rows_valid ? mu0 : rows_valid - 1)];
+      int mend = ao_off[m + 1] - mu_base;
       float ss = 0.f;
 #pragma unroll
       for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
@@ -472,9 +475,9 @@ struct PanelJob {
             for (int s = 0; s < slices; ++s) d[s * slice_elems] = take_slice(v, f);
           }
           if (mu + 1 == mend || cc + j == kEpiCols - 1 || mu + 1 == rows_valid) {  // warp-uniform
-            flush_norm(ss, base_key < 0 ? -1 : base_key + m * npa, norm2, lane);
+            flush_norm(ss, base_key < 0 ? -1 : base_key + (m - m_base) * npa, norm2, lane);
             ss = 0.f;
-            if (mu + 1 == mend && m + 1 < n_at) mend = ao_off[++m + 1];
+            if (mu + 1 == mend && m + 1 < n_at) mend = ao_off[++m + 1] - mu_base;
           }
         }
       }
@@ -489,8 +492,9 @@ struct PanelJob {
       int pw = n0 / tk.nsig;
       int sp = n0 - pw * tk.nsig;
       int patom = atom_of_ri[tk.p0 + (pw < tk.npw ? pw : tk.npw - 1)];
-      long long pwbase = static_cast<long long>(tk.p0 + pw) * ldk + rb;
-      const int row_key = r_ok ? (s_local * n_at + tk.owner) * n_at : -1;
+      long long pwbase = static_cast<long long>(tk.p0 + pw - P0b) * ldk + rb;
+      // key of (sigma-atom, mu-atom = owner, RI atom patom) is row_key + patom
+      const int row_key = r_ok ? (s_local * nmc + (tk.owner - m_base)) * npa - pa0 : -1;
       float ss = 0.f;
 #pragma unroll
       for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
@@ -514,12 +518,12 @@ struct PanelJob {
             pwbase += ldk;
             const int pa = (pw < tk.npw) ? atom_of_ri[tk.p0 + pw] : -1;
             if (pa != patom || last) {  // warp-uniform
-              flush_norm(ss, row_key < 0 ? -1 : row_key + patom, norm2, lane);
+              flush_norm(ss, r_ok ? row_key + patom : -1, norm2, lane);
               ss = 0.f;
               patom = pa;
             }
           } else if (last) {
-            flush_norm(ss, row_key < 0 ? -1 : row_key + patom, norm2, lane);
+            flush_norm(ss, r_ok ? row_key + patom : -1, norm2, lane);
             ss = 0.f;
           }
         }
@@ -802,28 +806,48 @@ __global__ void k_gather_g(const double* __restrict__ g, int nao, const PanelTas
   }
 }
 
-// Transposed, split panel: PT[s][p_row0 + n][k] = slice s of panel[k][n]
-// (k < K, n < N; zero padding up to (npad, kmax)).  32x32 tiles via smem.
-__global__ void k_transpose_panel(const double* __restrict__ pool, const PanelTaskTC* __restrict__ tasks,
-                                  int kmax, int slices, long long slice_elems, int f16,
-                                  double scale, uint16_t* __restrict__ out) {
-  __shared__ double tile[32][33];
-  const PanelTaskTC tk = tasks[blockIdx.z];
-  const int npad = (tk.N + kTileN - 1) / kTileN * kTileN;
-  const int n0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  if (n0 >= npad || k0 >= kmax) return;
-  const double* p = pool + tk.panel_off;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int i = ty; i < 32; i += 8) {
-    const int k = k0 + i, nn = n0 + tx;
-    tile[i][tx] = (k < tk.K && nn < tk.N) ? p[static_cast<long long>(k) * tk.N + nn] : 0.0;
-  }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int nn = n0 + i, k = k0 + tx;
-    double v = scale * tile[tx][i];
-    const long long dst = static_cast<long long>(tk.p_row0 + nn) * kmax + k;
-    for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
+// Split, transposed owner panels straight from the stored 3c blocks.  The
+// panel of owner atom s is PT[slice][p_row0(s) + pw * n_ao(s) + s'][k] =
+// slice of scale * T[lambda_k, sigma = s', P = p0(s) + pw] (k over the
+// functions of the atoms sharing a kept block with s).  Kept block (A, B, P)
+// [lambda' in A][sigma' in B][P'] lands in
+//   panel B: row rowB + P' n(B) + sigma', column kB + lambda'
+//   panel A (A != B): row rowA + P' n(A) + lambda', column kA + sigma'
+// (T symmetric in its primary indices).  Consecutive threads take
+// consecutive columns of a row.  One CTA per kept block, striding; the
+// buffer is zeroed beforehand (padding and blocks not stored).
+__global__ void k_pt_scatter(const double* __restrict__ t3, const int* __restrict__ blk,
+                             const long long* __restrict__ off, const int* __restrict__ n_ao,
+                             const int* __restrict__ n_ri, const int* __restrict__ kept,
+                             long long n_kept, const long long* __restrict__ rowB,
+                             const int* __restrict__ kB, const long long* __restrict__ rowA,
+                             const int* __restrict__ kA, int kmax, int slices, long long slice_elems,
+                             int f16, double scale, uint16_t* __restrict__ out) {
+  for (long long kb = blockIdx.x; kb < n_kept; kb += gridDim.x) {
+    const int b = kept[kb];
+    const int A = blk[3 * b], B = blk[3 * b + 1], p = blk[3 * b + 2];
+    const int na = n_ao[A], nb = n_ao[B], np = n_ri[p];
+    const double* x = t3 + off[b];
+    const long long n = static_cast<long long>(na) * nb * np;
+    // panel B: i = (P' nb + sigma') na + lambda'
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      const int al = static_cast<int>(i % na);
+      const long long r = i / na;  // P' nb + sigma'
+      const int be = static_cast<int>(r % nb), pl = static_cast<int>(r / nb);
+      double v = scale * x[(static_cast<long long>(al) * nb + be) * np + pl];
+      const long long dst = (rowB[kb] + r) * kmax + kB[kb] + al;
+      for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
+    }
+    if (A == B) continue;
+    // panel A: i = (P' na + lambda') nb + sigma'
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      const int be = static_cast<int>(i % nb);
+      const long long r = i / nb;  // P' na + lambda'
+      const int al = static_cast<int>(r % na), pl = static_cast<int>(r / na);
+      double v = scale * x[(static_cast<long long>(al) * nb + be) * np + pl];
+      const long long dst = (rowA[kb] + r) * kmax + kA[kb] + be;
+      for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
+    }
   }
 }
 
@@ -832,15 +856,15 @@ __global__ void k_transpose_panel(const double* __restrict__ pool, const PanelTa
 // blocks and the (slab, tile) pairs they touch; queue the filtered nonzero
 // ones (norm < thr) for zeroing.
 __global__ void k_slices_block_flags(const int* __restrict__ ri_off, int rowoff, int pa0, int npa,
-                                     int n_at, int ns, double thr, const float* __restrict__ norm2,
+                                     int nmc, int ns, double thr, const float* __restrict__ norm2,
                                      unsigned char* __restrict__ blockflag,
                                      unsigned char* __restrict__ tileflag, int ntile, int tile_rows,
                                      int* __restrict__ zlist, int* __restrict__ zcount) {
-  const long long nblk = static_cast<long long>(ns) * n_at * npa;
+  const long long nblk = static_cast<long long>(ns) * nmc * npa;
   for (long long w = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; w < nblk;
        w += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int pl = static_cast<int>(w % npa);
-    const long long t = w / npa;  // sl * n_at + m
+    const long long t = w / npa;  // sl * nmc + (m - m0)
     const double nrm = sqrt(static_cast<double>(norm2[w]));
     const bool kept = !(nrm < thr);
     const bool nz = kept && nrm > 0.0;
@@ -861,7 +885,7 @@ __global__ void k_slices_zero_blocks(uint16_t* __restrict__ Z, int slices, long 
                                      long long ldk, int rowoff, const int* __restrict__ ri_off,
                                      const int* __restrict__ ao_off, const int* __restrict__ n_ao,
                                      int s0, const long long* __restrict__ seg, int pa0, int npa,
-                                     int n_at, const int* __restrict__ zlist,
+                                     int m0, int nmc, int mu0, const int* __restrict__ zlist,
                                      const int* __restrict__ zcount) {
   const int lane = threadIdx.x & 31;
   const int nq = *zcount;
@@ -870,12 +894,12 @@ __global__ void k_slices_zero_blocks(uint16_t* __restrict__ Z, int slices, long 
     const long long w = zlist[q];
     const int pl = static_cast<int>(w % npa);
     const long long t = w / npa;
-    const int m = static_cast<int>(t % n_at);
-    const int sl = static_cast<int>(t / n_at);
+    const int m = m0 + static_cast<int>(t % nmc);
+    const int sl = static_cast<int>(t / nmc);
     const int nsig = n_ao[s0 + sl];
     const int p = pa0 + pl;
     const int rows0 = ri_off[p] - rowoff, nrows = ri_off[p + 1] - ri_off[p];
-    const long long c0 = seg[sl] + static_cast<long long>(ao_off[m]) * nsig;
+    const long long c0 = seg[sl] + static_cast<long long>(ao_off[m] - mu0) * nsig;
     const int ncols = n_ao[m] * nsig;
     for (int r = 0; r < nrows; ++r)
       for (int c = lane; c < ncols; c += 32)
@@ -901,19 +925,24 @@ __device__ __forceinline__ void zero_run(uint16_t* p, long long n) {
 // the segment when lo[Q] < 0), which includes the padding mu >= n_AO.  One
 // CTA per (Q, s) pair, striding.
 __global__ void k_zero_unwritten_y(uint16_t* __restrict__ Y, int slices, long long slice_elems,
-                                   long long ldk, int nri, int ns, const long long* __restrict__ seg,
-                                   const int* __restrict__ n_ao, int s0,
-                                   const int* __restrict__ ao_off, int naop,
+                                   long long ldk, int Q0, int qrow, int ns,
+                                   const long long* __restrict__ seg, const int* __restrict__ n_ao,
+                                   int s0, const int* __restrict__ ao_off, int m0, int m1, int Lc,
                                    const int* __restrict__ lo, const int* __restrict__ hi) {
-  const long long npair = static_cast<long long>(nri) * ns;
+  const long long npair = static_cast<long long>(qrow) * ns;
+  const int mu0 = ao_off[m0];
   for (long long w = blockIdx.x; w < npair; w += gridDim.x) {
-    const int q = static_cast<int>(w / ns), sl = static_cast<int>(w % ns);
+    const int ql = static_cast<int>(w / ns), sl = static_cast<int>(w % ns);
+    const int q = Q0 + ql;
     const int nsig = n_ao[s0 + sl];
-    const long long L = static_cast<long long>(naop) * nsig;
-    const long long a = lo[q] < 0 ? L : static_cast<long long>(ao_off[lo[q]]) * nsig;
-    const long long b = lo[q] < 0 ? L : static_cast<long long>(ao_off[hi[q] + 1]) * nsig;
+    const long long L = static_cast<long long>(Lc) * nsig;
+    // covering owners inside the chunk [m0, m1)
+    const int a0 = lo[q] < 0 ? m1 : max(lo[q], m0);
+    const int a1 = lo[q] < 0 ? m0 - 1 : min(hi[q], m1 - 1);
+    const long long a = a0 > a1 ? L : static_cast<long long>(ao_off[a0] - mu0) * nsig;
+    const long long b = a0 > a1 ? L : static_cast<long long>(ao_off[a1 + 1] - mu0) * nsig;
     for (int sc = 0; sc < slices; ++sc) {
-      uint16_t* base = Y + sc * slice_elems + static_cast<long long>(q) * ldk + seg[sl];
+      uint16_t* base = Y + sc * slice_elems + static_cast<long long>(ql) * ldk + seg[sl];
       zero_run(base, a);
       zero_run(base + b, L - b);
     }
@@ -1096,12 +1125,13 @@ void launch_plan_units(const int* tasks, const int* counts, const long long* kac
                                                w.start, w.u_tile, w.u_first, w.u_count);
 }
 
-void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int nri, int ns,
-                             const long long* seg, const int* n_ao, int s0, const int* ao_off,
-                             int naop, const int* lo, const int* hi, cudaStream_t st) {
-  if (nri == 0 || ns == 0) return;
+void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int Q0, int qrow,
+                             int ns, const long long* seg, const int* n_ao, int s0, const int* ao_off,
+                             int m0, int m1, int Lc, const int* lo, const int* hi, cudaStream_t st) {
+  if (qrow == 0 || ns == 0) return;
   tc::k_zero_unwritten_y<<<152 * 16, 256, 0, st>>>(static_cast<uint16_t*>(Y), slices, slice_elems, ldk,
-                                                   nri, ns, seg, n_ao, s0, ao_off, naop, lo, hi);
+                                                   Q0, qrow, ns, seg, n_ao, s0, ao_off, m0, m1, Lc, lo,
+                                                   hi);
 }
 
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
@@ -1214,10 +1244,10 @@ void tc_set_stall_test(int on) { g_stall_test = on; }
 
 int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, const CUtensorMap& my,
                   const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,
-                  const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
-                  double* chi, int flush_k, int* err_flag, cudaStream_t st) {
+                  const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int Q0,
+                  int qrow, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st) {
   tc::ChiJob job{tile_list, n_tiles, nullptr, nullptr, tasks, counts, max_slab, slab_k0, slab_len, nqt,
-                 P0, prow, nri, chi, out_scale, nullptr};
+                 P0, prow, nri, Q0, qrow, chi, out_scale, nullptr};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
@@ -1225,10 +1255,10 @@ int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap&
                         const CUtensorMap& my, const int* unit_tile, const int* unit_first,
                         const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
                         const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
-                        int P0, int prow, int nri, int nqt, double* chi, int flush_k, int* err_flag,
-                        cudaStream_t st) {
+                        int P0, int prow, int nri, int Q0, int qrow, int nqt, double* chi, int flush_k,
+                        int* err_flag, cudaStream_t st) {
   tc::ChiJob job{unit_tile, n_units, unit_first, unit_count, tasks, counts, max_slab, slab_k0, slab_len,
-                 nqt, P0, prow, nri, chi, out_scale, n_units_dev};
+                 nqt, P0, prow, nri, Q0, qrow, chi, out_scale, n_units_dev};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
@@ -1237,10 +1267,11 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
                     int mode, int rows_valid, void* out, long long slice_elems, long long ldk, int P0b,
                     const long long* rowbase, const int* rowmul, const int* row_slocal, float* norm2,
                     const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
-                    int pa0, int flush_k, int* err_flag, cudaStream_t st) {
+                    int pa0, int mu_base, int m_base, int nmc, int flush_k, int* err_flag,
+                    cudaStream_t st) {
   tc::PanelJob job{tiles, n_tiles, tasks, mode, rows_valid, static_cast<uint16_t*>(out), slice_elems,
                    ldk, P0b, rowbase, rowmul, row_slocal, norm2, atom_of_ri, atom_of_ao, ao_off, n_at,
-                   npa, pa0, slices, f16, unscale, out_scale};
+                   npa, pa0, slices, mu_base, m_base, nmc, f16, unscale, out_scale};
   // mode 0: the panel rows are the A operand
   if (mode == 0) return launch_persistent(slices, f16, mp, mg, job, flush_k, err_flag, st);
   return launch_persistent(slices, f16, mg, mp, job, flush_k, err_flag, st);
@@ -1258,36 +1289,36 @@ void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int nta
                                        slices, slice_elems, f16, scale, static_cast<uint16_t*>(out));
 }
 
-void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
-                             int kmax, int slices, long long slice_elems, int f16, double scale,
-                             void* out, cudaStream_t st) {
-  if (ntasks == 0) return;
-  for (int z0 = 0; z0 < ntasks; z0 += 65535) {
-    const int nz = ntasks - z0 < 65535 ? ntasks - z0 : 65535;
-    dim3 grid((max_npad + 31) / 32, (kmax + 31) / 32, nz);
-    tc::k_transpose_panel<<<grid, 256, 0, st>>>(pool, tasks + z0, kmax, slices, slice_elems, f16, scale,
-                                                static_cast<uint16_t*>(out));
-  }
+void launch_pt_scatter(const double* t3, const int* blk, const long long* off, const int* n_ao,
+                       const int* n_ri, const int* kept, long long n_kept, const long long* rowB,
+                       const int* kB, const long long* rowA, const int* kA, int kmax, int slices,
+                       long long slice_elems, int f16, double scale, void* out, cudaStream_t st) {
+  if (n_kept == 0) return;
+  const long long grid = n_kept < 152LL * 64 ? n_kept : 152LL * 64;
+  tc::k_pt_scatter<<<static_cast<unsigned>(grid), 128, 0, st>>>(t3, blk, off, n_ao, n_ri, kept, n_kept,
+                                                               rowB, kB, rowA, kA, kmax, slices,
+                                                               slice_elems, f16, scale,
+                                                               static_cast<uint16_t*>(out));
 }
 
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
                                 const int* ri_off, const int* ao_off, const int* n_ao, int s0,
-                                int ns, const long long* seg, int pa0, int npa, int n_at,
-                                double thr, const float* norm2, unsigned char* blockflag,
+                                int ns, const long long* seg, int pa0, int npa, int m0, int nmc,
+                                int mu0, double thr, const float* norm2, unsigned char* blockflag,
                                 unsigned char* tileflag, int ntile, int tile_rows, int* zlist,
                                 int* zcount, cudaStream_t st) {
-  const long long nblk = static_cast<long long>(ns) * n_at * npa;
+  const long long nblk = static_cast<long long>(ns) * nmc * npa;
   if (nblk == 0) return;
   cudaMemsetAsync(zcount, 0, sizeof(int), st);
   long long blocks = (nblk + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   tc::k_slices_block_flags<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-      ri_off, rowoff, pa0, npa, n_at, ns, thr, norm2, blockflag, tileflag, ntile, tile_rows, zlist,
+      ri_off, rowoff, pa0, npa, nmc, ns, thr, norm2, blockflag, tileflag, ntile, tile_rows, zlist,
       zcount);
   // many warps: each queued block is a few kilobytes of scattered rows
   tc::k_slices_zero_blocks<<<152 * 64, 256, 0, st>>>(static_cast<uint16_t*>(Z), slices, slice_elems, ldk,
-                                                  rowoff, ri_off, ao_off, n_ao, s0, seg, pa0, npa, n_at,
-                                                  zlist, zcount);
+                                                  rowoff, ri_off, ao_off, n_ao, s0, seg, pa0, npa, m0,
+                                                  nmc, mu0, zlist, zcount);
 }
 
 }  // namespace gw

@@ -31,15 +31,16 @@ double pow2_scale(double bound);
 // matrix (row stride ld), on the stream.
 void launch_absmax_rowsum(const double* a, long long ld, int rows, int cols, double* out2,
                           cudaStream_t st);
-// Step C on the tensor cores: chi[P0 + p][q] -= out_scale * sum over the
-// tile's slabs of X[p][k] Y[q][k] with `slices` slices; one work item per
-// entry of tile_list (tile = pt * nqt + qt, 128 x 128).  err_flag != 0 after
+// Step C on the tensor cores: chi[P0 + p][Q0 + q] -= out_scale * sum over
+// the tile's slabs of X[p][k] Y[q][k] with `slices` slices (p < prow,
+// q < qrow); one work item per entry of tile_list (tile = pt * nqt + qt,
+// 128 x 128).  err_flag != 0 after
 // the kernel means a bounded wait gave up.  Returns 0 or a negative setup
 // error (-4: unsupported slice count / format).
 int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, const CUtensorMap& my,
                   const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,
-                  const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int nqt,
-                  double* chi, int flush_k, int* err_flag, cudaStream_t st);
+                  const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int Q0,
+                  int qrow, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st);
 // Step C over work units that split tiles along K: unit u computes tile
 // unit_tile[u] over list entries [unit_first[u], unit_first[u] + unit_count[u])
 // of that tile's task list and adds into chi with FP64 atomics.  The number
@@ -49,8 +50,8 @@ int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap&
                         const CUtensorMap& my, const int* unit_tile, const int* unit_first,
                         const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
                         const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
-                        int P0, int prow, int nri, int nqt, double* chi, int flush_k, int* err_flag,
-                        cudaStream_t st);
+                        int P0, int prow, int nri, int Q0, int qrow, int nqt, double* chi, int flush_k,
+                        int* err_flag, cudaStream_t st);
 // Device scratch of launch_plan_units: per tile (ntiles) ucnt, uoff; per unit
 // (capacity ntiles * nslab) t_tile, t_first, t_count, t_key, u_tile, u_first,
 // u_count; per slab (nslab) hist, start; and the counters n_units,
@@ -71,20 +72,26 @@ void launch_plan_units(const int* tasks, const int* counts, const long long* kac
 // 1 writes Y, as slices of out_scale * (unscale * accumulator), and
 // accumulates the squared atom-block norms of unscale * accumulator.  Tile
 // entries (task, i, j): mode 0 i = panel-row tile, j = G-row tile; mode 1
-// i = G-row tile, j = panel-row tile.
+// i = G-row tile, j = panel-row tile.  The G rows are local to a chunk of
+// mu-atoms (nmc atoms from m_base, AOs from mu_base); norm2 is
+// [ns][nmc][npa] over the RI atoms [pa0, pa0 + npa) of the output's rows,
+// which start at RI function P0b.
 int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const CUtensorMap& mg,
                     const CUtensorMap& mp, const int4* tiles, int n_tiles, const PanelTaskTC* tasks,
                     int mode, int rows_valid, void* out, long long slice_elems, long long ldk, int P0b,
                     const long long* rowbase, const int* rowmul, const int* row_slocal, float* norm2,
                     const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
-                    int pa0, int flush_k, int* err_flag, cudaStream_t st);
+                    int pa0, int mu_base, int m_base, int nmc, int flush_k, int* err_flag,
+                    cudaStream_t st);
 // Zero the part of the step-B operand Y that step B does not write: for each
-// RI row q and batch atom s, the mu outside the owner atoms [lo[q], hi[q]]
-// whose panel windows cover q (the whole segment when lo[q] < 0).  Valid
-// when the owners covering each q form one contiguous range.
-void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int nri, int ns,
-                             const long long* seg, const int* n_ao, int s0, const int* ao_off,
-                             int naop, const int* lo, const int* hi, cudaStream_t st);
+// Y row (RI function Q0 + ql, ql < qrow) and batch atom s, the chunk-local mu
+// (chunk atoms [m0, m1), segment Lc functions) outside the owner atoms
+// [lo[q], hi[q]] whose panel windows cover q (the whole segment when none of
+// them lies in the chunk).  Valid when the owners covering each q form one
+// contiguous range.
+void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long long ldk, int Q0, int qrow,
+                             int ns, const long long* seg, const int* n_ao, int s0, const int* ao_off,
+                             int m0, int m1, int Lc, const int* lo, const int* hi, cudaStream_t st);
 // scale * FP64 [rows][cols] (row stride ld) -> `slices` slices [S][rows][kpad],
 // zero-padded in k.
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,
@@ -92,17 +99,22 @@ void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpa
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
                      int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
                      long long slice_elems, int f16, double scale, void* out, cudaStream_t st);
-void launch_transpose_panels(const double* pool, const PanelTaskTC* tasks, int ntasks, int max_npad,
-                             int kmax, int slices, long long slice_elems, int f16, double scale,
-                             void* out, cudaStream_t st);
+// Split, transposed owner panels [slices][rows][kmax] straight from the
+// kept 3c blocks (see k_pt_scatter); out must be zeroed beforehand.
+void launch_pt_scatter(const double* t3, const int* blk, const long long* off, const int* n_ao,
+                       const int* n_ri, const int* kept, long long n_kept, const long long* rowB,
+                       const int* kB, const long long* rowA, const int* kA, int kmax, int slices,
+                       long long slice_elems, int f16, double scale, void* out, cudaStream_t st);
 // Atom-block filter of an operand (X or Y) from the squared norms its panel
 // job accumulated: blockflag = kept and nonzero, tileflag per (sigma-atom,
-// mu-atom, row tile) touched, and the filtered nonzero blocks zeroed in every
-// slice.  zlist (ns * n_at * npa ints) and zcount (one int) are scratch.
+// mu-atom of the chunk [m0, m0 + nmc), row tile) touched, and the filtered
+// nonzero blocks zeroed in every slice (K offsets relative to the chunk's
+// first AO mu0).  zlist (ns * nmc * npa ints) and zcount (one int) are
+// scratch.
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,
                                 const int* ri_off, const int* ao_off, const int* n_ao, int s0,
-                                int ns, const long long* seg, int pa0, int npa, int n_at,
-                                double thr, const float* norm2, unsigned char* blockflag,
+                                int ns, const long long* seg, int pa0, int npa, int m0, int nmc,
+                                int mu0, double thr, const float* norm2, unsigned char* blockflag,
                                 unsigned char* tileflag, int ntile, int tile_rows, int* zlist,
                                 int* zcount, cudaStream_t st);
 

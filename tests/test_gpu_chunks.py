@@ -1,0 +1,96 @@
+"""The tensor-core route with its operands cut into 2-D batches (sigma-atom
+batches x mu-atom chunks, each chunk's Y restricted to the RI window of its
+atoms' 3c blocks), and the useful-flop count of every route against the
+oracle's own count (oracle.chi.useful_flops_dense)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import chi as oc  # noqa: E402
+from synth import make_case  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_09857_gb300 as pkg
+
+    return pkg
+
+
+def _run(pkg, case, precision, thr, options=None):
+    with pkg.Context(0) as ctx:
+        for k, v in (options or {}).items():
+            ctx.set_option(k, v)
+        ctx.load_case(case)
+        got = ctx.chi_tau(thr, precision).cpu().numpy()
+        return got, ctx.stats()
+
+
+def _check(got, ref, tol):
+    for j in range(ref.shape[0]):
+        r, g = ref[j], got[j]
+        if not np.any(r):
+            assert not np.any(g)
+            continue
+        rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+        el = np.abs(g - r).max() / np.abs(r).max()
+        assert rel <= tol and el <= tol, (j, rel, el)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp16x3", 1e-6), ("bf16x6", 1e-6)])
+@pytest.mark.parametrize("thr", [1e-9, 1e-3])
+@pytest.mark.parametrize("chunk,batch_atoms", [(5, 0), (9, 3), (1, 2)])
+def test_chunked_batches_match_oracle(lib, precision, tol, thr, chunk, batch_atoms):
+    """mu chunks of 1, 5 and 9 atoms (ragged last chunk, windows cut inside
+    the ribbon), with and without small owner batches: chi within the form's
+    tolerance of the oracle, and the same useful-flop count as one chunk."""
+    case = make_case("ribbon28", n_tau=3)
+    ref = oc.chi_dense(case, thr=thr)
+    opts = {"mu_chunk_atoms": chunk}
+    if batch_atoms:
+        opts["batch_atoms"] = batch_atoms
+    got, st = _run(lib, case, precision, thr, opts)
+    _check(got, ref, tol)
+    one, st1 = _run(lib, case, precision, thr)
+    assert st["n_batches"] > st1["n_batches"]
+    for k in ("flops_a", "flops_b", "flops_c"):
+        assert st[k] == pytest.approx(st1[k], rel=1e-12), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16x3"])
+@pytest.mark.parametrize("name,thr", [("ribbon28", 1e-9), ("ribbon28", 1e-3), ("benzene", 0.0)])
+def test_useful_flops_match_oracle_count(lib, precision, name, thr):
+    """The library's useful flops per step equal the oracle's count of the
+    atom-block products whose operands survive the filter, at every tau."""
+    case = make_case(name, n_tau=3)
+    with lib.Context(0) as ctx:
+        ctx.load_case(case)
+        for j in range(len(case.tau)):
+            ctx.chi_tau(thr, precision, j, 1)
+            st = ctx.stats()
+            # (a skipped batch's flops are not credited; none is skipped here)
+            assert st["batches_skipped"] == 0
+            fa, fb, fc = oc.useful_flops_dense(case, j, thr=thr)
+            assert st["flops_a"] == fa and st["flops_b"] == fb, (j, st["flops_a"], fa)
+            assert st["flops_c"] == pytest.approx(fc, rel=1e-12), (j, st["flops_c"], fc)
+
+
+def test_filtered_chunks_are_skipped(lib):
+    """At a threshold that filters the Green's-function blocks between the
+    ribbon's two ends, batches whose X or Y is entirely filtered are skipped,
+    and chi still matches the oracle."""
+    case = make_case("ribbon60", n_tau=2)
+    thr = 3e-2
+    ref = oc.chi_dense(case, thr=thr)
+    got, st = _run(lib, case, "fp16x3", thr, {"mu_chunk_atoms": 6, "batch_atoms": 6})
+    _check(got, ref, 1e-6)
+    assert st["batches_skipped"] > 0

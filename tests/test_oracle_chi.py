@@ -187,3 +187,46 @@ def test_block_oracle_matches_dense(thr):
             blk = bo.block(1, p, q, cache)
             ref = dense[ri[p]:ri[p + 1], ri[q]:ri[q + 1]]
             assert np.allclose(blk, ref, rtol=1e-11, atol=1e-12 * np.abs(dense).max()), (p, q)
+
+
+@pytest.mark.parametrize("thr", [0.0, 1e-3])
+def test_useful_flops_two_routes_and_closed_form(thr):
+    """The useful-flop count of one tau point from the dense route equals the
+    count from the block oracle's slices, and at thr 0 (nothing filtered,
+    every stored block kept) steps A and B each equal 2 n_AO times the
+    stored elements of both block orientations."""
+    case = make_case("ribbon28", n_tau=2, thr=1e-9)
+    dense = oc.useful_flops_dense(case, 1, thr=thr)
+    blocks = oc.useful_flops_blocks(oc.BlockOracle(case, thr=thr), 1)
+    assert dense == pytest.approx(blocks, rel=1e-14)
+    if thr == 0.0:
+        s = case.system
+        b = case.t3c.blocks
+        elems = s.n_ao[b[:, 0]] * s.n_ao[b[:, 1]] * s.n_ri[b[:, 2]] * np.where(b[:, 0] == b[:, 1], 1, 2)
+        assert dense[0] == dense[1] == 2.0 * s.nao_total * float(np.sum(elems))
+
+
+def test_useful_flops_step_c_by_loops():
+    """F_C by explicit loops over (mu-atom, sigma-atom, p <= q) on a 3-atom
+    chain at a threshold that drops some M/N blocks."""
+    case = make_case("chain_CHCH", n_tau=2, thr=0.0)
+    thr = 1e-2
+    s = case.system
+    ao, ri = oc.offsets(s.n_ao), oc.offsets(s.n_ri)
+    t = oc.dense_three_center(s.n_ao, s.n_ri, case.t3c.blocks, case.t3c.offsets, case.t3c.data, thr)
+    go, gv = oc.greens(case.C, case.eps, case.n_occ, case.mu_fermi, case.tau[1])
+    go, gv = oc.filter_sym_2d(go, ao, thr), oc.filter_sym_2d(gv, ao, thr)
+    m = oc.filter_3idx(np.einsum("ml,lsp->msp", go, t), [ao, ao, ri], thr)
+    n = oc.filter_3idx(np.einsum("mnq,ns->msq", t, gv), [ao, ao, ri], thr)
+    n_at = s.n_atoms
+    fc = 0.0
+    for a in range(n_at):
+        for b in range(n_at):
+            for p in range(n_at):
+                for q in range(p, n_at):
+                    mb = m[ao[a]:ao[a + 1], ao[b]:ao[b + 1], ri[p]:ri[p + 1]]
+                    nb = n[ao[a]:ao[a + 1], ao[b]:ao[b + 1], ri[q]:ri[q + 1]]
+                    if np.any(mb) and np.any(nb):
+                        fc += 2.0 * s.n_ao[a] * s.n_ao[b] * s.n_ri[p] * s.n_ri[q]
+    assert oc.useful_flops_dense(case, 1, thr=thr)[2] == fc
+    assert fc < oc.useful_flops_dense(case, 1, thr=0.0)[2]  # the filter dropped some blocks

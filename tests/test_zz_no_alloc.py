@@ -75,6 +75,11 @@ def test_noalloc_requires_panels_and_rejects_bad_arguments(pkg):
         with pytest.raises(_lib.GwError) as e:
             _lib.gw_chi_tau_noalloc(ctx.ctx, 0, 0.0, out.data_ptr())
         assert e.value.code == -2
+        # the tensor-core route builds no FP64 panels
+        ctx.chi_tau(0.0, "fp16x3", 0, 1)
+        with pytest.raises(_lib.GwError) as e:
+            _lib.gw_chi_tau_noalloc(ctx.ctx, 0, 0.0, out.data_ptr())
+        assert e.value.code == -2
         ctx.chi_tau(0.0, "fp64", 0, 1)
         with pytest.raises(_lib.GwError) as e:
             _lib.gw_chi_tau_noalloc(ctx.ctx, 99, 0.0, out.data_ptr())

@@ -391,6 +391,9 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
  *                  (default 40e9)
  *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)
+ *   "panel_staged" two-slice forms (FP16x3, BF16x3): 1 (default) steps A/B
+ *                  stage each finished tile in shared memory and write whole
+ *                  runs of X and Y; 0 per-element stores from registers
  *   "mu_chunk_atoms" split forms: mu-atoms per chunk of the 2-D operand
  *                  batches (0 = automatic: the fewest equal chunks for which
  *                  one sigma-atom's X and Y fit in batch_bytes / 8; one chunk

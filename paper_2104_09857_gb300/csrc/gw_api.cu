@@ -986,6 +986,13 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = c_event_pair(ctx, 2 * batch_idx + 1, &ea0, &ea1))) return rc;
   GW_TRY(cudaEventRecord(ea0, ctx->stream));
 
+  int* d_nao_a;
+  if ((rc = upload(ctx, "n_ao_b", ctx->n_ao, &d_nao_a))) return rc;
+  // the staged epilogue (two slices) writes whole runs of X and Y: its tiles
+  // start at pw boundaries (and at owner atoms for step B's rows), which
+  // needs every atom's function count to be at most one tile
+  bool staged = ctx->panel_staged && slices == 2;
+  for (int a = 0; a < n_at && staged; ++a) staged = ctx->n_ao[a] <= tile;
   // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu of the chunk ----
   {
     const int rows_a = (b.nmu + tile - 1) / tile * tile;
@@ -997,10 +1004,22 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       t.g_row0 = (int)ta.size() * rows_a;
       t.seg = b.seg[s - b.s0];
       t.s_local = s - b.s0;
-      const int ntn = (t.N + tile - 1) / tile;
-      for (int nt = 0; nt < ntn; ++nt)
-        for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), nt, mt, 0));
-      issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+      if (staged) {
+        // panel rows from pw boundaries: (tile / nsig) whole runs per tile
+        const int meff = tile / t.nsig * t.nsig;
+        int ntn = 0;
+        for (int ra = 0; ra < t.N; ra += meff, ++ntn)
+          for (int mt = 0; mt < rows_a / tile; ++mt) {
+            const int rv = std::min(meff, t.N - ra), cv = std::min(tile, b.nmu - mt * tile);
+            tiles.push_back(make_int4((int)ta.size(), ra, mt * tile, (rv << 16) | cv));
+          }
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+      } else {
+        const int ntn = (t.N + tile - 1) / tile;
+        for (int nt = 0; nt < ntn; ++nt)
+          for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), nt, mt, 0));
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+      }
       ta.push_back(t);
     }
     if (!ta.empty()) {
@@ -1017,12 +1036,18 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       CUtensorMap mg;
       if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step A)");
-      if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
-                              (int)tiles.size(), d_ta, 0, b.nmu, xs,
-                              (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
-                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, npa, pa0,
-                              b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream))
-        return fail(ctx, GW_ERR_CUDA, "tensor-core step A launch setup failed");
+      const int lrc =
+          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
+                                              (int)tiles.size(), d_ta, 0, xs, (long long)prow * Kb, Kb,
+                                              b.P0, b.Lc, 0, b.s0, nullptr, bx2, ctx->d_atom_of_ri,
+                                              ctx->d_atom_of_ao, ctx->d_ao_off, ctx->d_ri_off, d_nao_a,
+                                              npa, pa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream)
+                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
+                                       (int)tiles.size(), d_ta, 0, b.nmu, xs,
+                                       (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
+                                       ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, npa,
+                                       pa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream);
+      if (lrc) return fail(ctx, GW_ERR_CUDA, "tensor-core step A launch setup failed");
       GW_CHECK_LAUNCH();
       ctx->stats.kernel_launches += 2;
     }
@@ -1034,15 +1059,34 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     const int rows_b = (R + tile - 1) / tile * tile;
     std::vector<gw::PanelTaskTC> tb;
     std::vector<int4> tiles;
+    // staged: batch rows in groups of whole owner atoms, at most one tile each
+    std::vector<std::pair<int, int>> groups;
+    if (staged)
+      for (int s = b.s0; s < b.s1;) {
+        const int g0 = ctx->ao_off[s] - r0;
+        while (s < b.s1 && ctx->ao_off[s + 1] - r0 - g0 <= tile) ++s;
+        groups.push_back({g0, ctx->ao_off[s] - r0 - g0});
+      }
     for (int m = b.m0; m < b.m1; ++m) {
       gw::PanelTaskTC t = ctx->pt_tasks[m];
       if (t.K == 0) continue;
       t.aom -= b.mu0;  // chunk-local first AO of the panel's owner
       t.g_row0 = (int)tb.size() * rows_b;
-      const int ntn = (t.N + tile - 1) / tile;
-      for (int nt = 0; nt < ntn; ++nt)
-        for (int mt = 0; mt < rows_b / tile; ++mt) tiles.push_back(make_int4((int)tb.size(), mt, nt, 0));
-      issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_b / tile) * ntn;
+      if (staged) {
+        const int meff = tile / t.nsig * t.nsig;  // whole runs of the owner's functions
+        int ntn = 0;
+        for (int rb = 0; rb < t.N; rb += meff, ++ntn)
+          for (const auto& g : groups) {
+            const int cv = std::min(meff, t.N - rb);
+            tiles.push_back(make_int4((int)tb.size(), g.first, rb, (g.second << 16) | cv));
+          }
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * groups.size() * ntn;
+      } else {
+        const int ntn = (t.N + tile - 1) / tile;
+        for (int nt = 0; nt < ntn; ++nt)
+          for (int mt = 0; mt < rows_b / tile; ++mt) tiles.push_back(make_int4((int)tb.size(), mt, nt, 0));
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_b / tile) * ntn;
+      }
       tb.push_back(t);
     }
     std::vector<long long> rowbase(R);
@@ -1072,12 +1116,18 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       CUtensorMap mg;
       if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
-      if (gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
-                              (int)tiles.size(), d_tb, 1, R, ys,
-                              (long long)qrow * Kb, Kb, b.Q0, d_rowbase, d_rowmul, d_rowsl, by2,
-                              ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, nqa, qa0,
-                              b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream))
-        return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
+      const int lrc =
+          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
+                                              (int)tiles.size(), d_tb, 1, ys, (long long)qrow * Kb, Kb,
+                                              b.Q0, b.Lc, r0, b.s0, d_rowbase, by2, ctx->d_atom_of_ri,
+                                              ctx->d_atom_of_ao, ctx->d_ao_off, ctx->d_ri_off, d_nao_a,
+                                              nqa, qa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream)
+                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
+                                       (int)tiles.size(), d_tb, 1, R, ys,
+                                       (long long)qrow * Kb, Kb, b.Q0, d_rowbase, d_rowmul, d_rowsl, by2,
+                                       ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, nqa,
+                                       qa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream);
+      if (lrc) return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
       GW_CHECK_LAUNCH();
       ctx->stats.kernel_launches += 2;
     }
@@ -1658,6 +1708,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
   if (!strcmp(key, "flush_k")) {
     if (!(value >= 16 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [16, 2^30]");
     ctx->flush_k = (int)value;
+    return GW_OK;
+  }
+  if (!strcmp(key, "panel_staged")) {
+    if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "panel_staged must be 0 or 1");
+    ctx->panel_staged = (int)value;
     return GW_OK;
   }
   if (!strcmp(key, "mu_chunk_atoms")) {

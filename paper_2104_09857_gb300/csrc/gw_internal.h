@@ -241,6 +241,9 @@ struct gw_ctx {
   // mu-atoms per chunk of the tensor-core route's 2-D batches (0: the fewest
   // equal chunks that keep one owner's operands within budget / 8)
   int mu_chunk_atoms = 0;
+  // two-slice forms: steps A/B stage each finished tile in shared memory and
+  // write whole runs of X and Y (0: per-element stores from registers)
+  int panel_staged = 1;
 
   // named device work buffers (grown on demand) and the step timing events
   // of this context; a context is used by one host thread at a time

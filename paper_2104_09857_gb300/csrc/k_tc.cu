@@ -231,14 +231,33 @@ constexpr int kStgCols = 8;
 constexpr int kStgPitch = kStgCols + 1;
 constexpr int kStgBytes = 32 * kStgPitch * 4;
 
-template <int S>
+// Whole-tile staging (jobs with kTileStaging): the finished 128 x 128 FP32
+// tile, row pitch kTilePitch floats (no bank conflicts on column reads).
+constexpr int kTilePitch = kTileN + 1;
+constexpr int kTileStgBytes = kTileM * kTilePitch * 4;
+
+template <int S, class Job>
 struct Smem {
-  static constexpr int kStages = (S == 2) ? 3 : 2;
+  // a job that stages whole tiles keeps two operand stages to make room
+  static constexpr int kStages = Job::kTileStaging ? 2 : ((S == 2) ? 3 : 2);
   static constexpr int kTileBytes = kTileM * kStageK * 2;  // 16 KB, A and B alike
   static constexpr int kStageBytes = 2 * S * kTileBytes;
   static constexpr int kOperandBytes = kStages * kStageBytes;
-  static constexpr int kStagingBytes = kEpiWarps * kStgBytes;
+  static constexpr int kStagingBytes = Job::kTileStaging ? kTileStgBytes : kEpiWarps * kStgBytes;
   static constexpr int kTotal = kOperandBytes + kStagingBytes + 256 + 1024;
+};
+
+// What a tile-staging job's epilogue needs besides its registers: the staging
+// area, two barriers over the epilogue warps (tile staged by every warp;
+// tile written out by every warp), the abort flag, the warp's index among
+// the epilogue warps and the number of tiles this CTA has written so far.
+struct EpiCtx {
+  uint8_t* staging;
+  uint64_t* staged;
+  uint64_t* freed;
+  volatile int* abort;
+  int warp;
+  int tile_no;
 };
 
 // ---------------------------------------------------------------------------
@@ -255,11 +274,12 @@ struct ChiJob {
   const long long* slab_k0;
   const int* slab_len;
   int nqt, P0, prow, nri;
-  int Q0, qrow;     // Y rows are RI functions [Q0, Q0 + qrow)
-  double* chi;
+  int qlim;         // Y row ql adds into chi column Q0 + ql; written while ql < qlim = n_RI - Q0
+  double* chi;      // chi + Q0 (row stride nri)
   float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
   const int* n_dev; // optional: number of units in device memory (n_tiles = capacity)
   static constexpr bool kPeriodic = true;
+  static constexpr bool kTileStaging = false;
   static constexpr int kDrainHalves = 2;  // 96 registers: one 32-column load would spill
 
   struct Tile {
@@ -328,14 +348,15 @@ struct ChiJob {
       for (int j = 0; j < kStgCols; ++j) f[lane * kStgPitch + j] = acc[cc + j];
       __syncwarp();
       const int col = lane % kStgCols, sub = lane / kStgCols;
-      const int ql = T.yb + c0 + cc + col;  // Y row
-      const int q = Q0 + ql;
+      // Y row ql; rows past the Y operand read as zeros (TMA fill), so
+      // every ql < qlim may be written
+      const int q = T.yb + c0 + cc + col;
       if (unit_first) {
         // units of one tile may run concurrently when K is split
 #pragma unroll
         for (int i = 0; i < 32; i += kRowsPer) {
           const int p = T.ya + quad * 32 + i + sub;
-          if (p < prow && ql < qrow)
+          if (p < prow && q < qlim)
             atomicAdd(chi + static_cast<long long>(P0 + p) * nri + q,
                       -static_cast<double>(f[(i + sub) * kStgPitch + col] * out_scale));
         }
@@ -345,12 +366,12 @@ struct ChiJob {
 #pragma unroll
         for (int i = 0; i < 32 / kRowsPer; ++i) {
           const int p = T.ya + quad * 32 + kRowsPer * i + sub;
-          old[i] = (p < prow && ql < qrow) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
+          old[i] = (p < prow && q < qlim) ? chi[static_cast<long long>(P0 + p) * nri + q] : 0.0;
         }
 #pragma unroll
         for (int i = 0; i < 32 / kRowsPer; ++i) {
           const int p = T.ya + quad * 32 + kRowsPer * i + sub;
-          if (p < prow && ql < qrow)
+          if (p < prow && q < qlim)
             chi[static_cast<long long>(P0 + p) * nri + q] =
                 old[i] - static_cast<double>(f[(kRowsPer * i + sub) * kStgPitch + col] * out_scale);
         }
@@ -406,6 +427,7 @@ struct PanelJob {
   float unscale;              // 1 / (scale of Gg x scale of PT): true Z = acc * unscale
   float out_scale;            // scale of the Z slices
   static constexpr bool kPeriodic = false;
+  static constexpr bool kTileStaging = false;
   static constexpr int kDrainHalves = 1;
 
   struct Tile {
@@ -532,6 +554,200 @@ struct PanelJob {
   }
 };
 
+// Steps A / B with a staged epilogue (two slices only).  Tiles are aligned
+// to whole output runs:
+//   mode 0 (X): A operand = owner panel rows n = (pw, s'); a tile starts at a
+//     pw boundary and covers rv = (128 / nsig) nsig rows or the panel's rest,
+//     B operand = 128 G^occ rows mu (chunk-local).  For each of its pw the
+//     tile is the contiguous run X[P0 + pw][seg + mu0 nsig, + ncol nsig).
+//   mode 1 (Y): A operand = batch rows sigma, a group of whole owner atoms
+//     (<= 128 rows); B operand = panel rows n = (pw, mu') of atom tk.owner, a
+//     tile starting at a pw boundary with (128 / n_ao) n_ao rows or the rest.
+//     For each (owner s, pw) the tile is the contiguous run
+//     Y[pw - Q0][seg(s) + aom n(s), + n(owner) n(s)].
+// The 16 epilogue warps stage the finished tile (true values, FP32) in shared
+// memory, then together write it out (mode 0 as 16-byte vectors) and add the
+// squared Frobenius norms of its atom blocks into norm2, one atomic per
+// rectangle (mu-atom x RI atom in mode 0, owner x pw in mode 1).
+struct PanelStagedJob {
+  const int4* tiles;          // (task, A row offset, B row offset, rows_valid << 16 | cols_valid)
+  int n_tiles;
+  const PanelTaskTC* tasks;
+  int mode;
+  uint16_t* out;              // slices [2][slice_elems]
+  long long slice_elems, ldk;
+  int P0b;                    // first RI function of the output rows
+  int Lc;                     // mode 0: chunk segment length (X columns per s' run)
+  int row_ao0;                // mode 1: global AO of batch row 0
+  int s0b;                    // mode 1: first owner atom of the batch
+  const long long* rowbase;   // mode 1, per batch row: seg(s) + sigma'
+  float* norm2;               // [ns][nmc][npa]
+  const int* atom_of_ri;
+  const int* atom_of_ao;
+  const int* ao_off;
+  const int* ri_off;
+  const int* n_ao;
+  int npa, pa0, mu_base, m_base, nmc;
+  int f16;
+  float unscale, out_scale;
+  static constexpr bool kPeriodic = false;
+  static constexpr bool kTileStaging = true;
+  static constexpr int kDrainHalves = 1;
+
+  struct Tile {
+    int ya, yb, ksteps, task, ra, rb, rv, cv;
+  };
+  __device__ Tile tile(int t) const {
+    const int4 e = tiles[t];
+    const PanelTaskTC& tk = tasks[e.x];
+    Tile T;
+    T.task = e.x;
+    T.ra = e.y;
+    T.rb = e.z;
+    T.rv = e.w >> 16;
+    T.cv = e.w & 0xffff;
+    if (mode == 0) {
+      T.ya = tk.p_row0 + e.y;
+      T.yb = tk.g_row0 + e.z;
+    } else {
+      T.ya = tk.g_row0 + e.y;
+      T.yb = tk.p_row0 + e.z;
+    }
+    T.ksteps = tk.ksteps;
+    return T;
+  }
+  __device__ long long nsteps(const Tile& T) const { return T.ksteps; }
+  __device__ int items() const { return n_tiles; }
+  struct Iter {
+    int x;
+    __device__ void init(const PanelStagedJob*, const Tile&) { x = 0; }
+    __device__ int next() {
+      const int v = x;
+      x += kStageK;
+      return v;
+    }
+  };
+
+  __device__ static void pack_slices(float v, bool f, uint16_t& h0, uint16_t& h1) {
+    h0 = take_slice(v, f);
+    h1 = take_slice(v, f);
+  }
+  // Sum of squares over the staged rectangle rows [r0, r1) x cols [c0, c1),
+  // added into norm2[key] by lane 0 (all 32 lanes call).
+  __device__ static void rect_norm(const float* tile, int r0, int r1, int c0, int c1, int lane,
+                                   float* norm2, int key) {
+    const int w = c1 - c0, n = (r1 - r0) * w;
+    float ss = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float v = tile[(r0 + i / w) * kTilePitch + c0 + i % w];
+      ss += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
+  }
+
+  __device__ bool write_staged(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
+                               EpiCtx& ep) const {
+    float* tile = reinterpret_cast<float*>(ep.staging);
+    // the previous tile has been written out by every epilogue warp
+    if (ep.tile_no > 0 && !mbar_wait(ep.freed, static_cast<uint32_t>(ep.tile_no - 1) & 1u, ep.abort))
+      return false;
+    {
+      float* row = tile + (quad * 32 + lane) * kTilePitch + c0;
+#pragma unroll
+      for (int j = 0; j < kEpiCols; ++j) row[j] = acc[j] * unscale;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(ep.staged);
+    if (!mbar_wait(ep.staged, static_cast<uint32_t>(ep.tile_no) & 1u, ep.abort)) return false;
+    const PanelTaskTC& tk = tasks[T.task];
+    const bool f = f16 != 0;
+    const int tid = ep.warp * 32 + lane;
+    constexpr int kThr = kEpiWarps * 32;
+    if (mode == 0) {
+      const int nsig = tk.nsig;
+      const int ng = T.rv / nsig;               // pw runs in the tile
+      const int pw0 = T.ra / nsig;
+      const int mu0 = T.rb;                     // chunk-local
+      const int ncol = min(kTileN, Lc - mu0);   // X columns written (zeros past cv)
+      const int units = ncol * nsig / 8;        // 8-element vectors per run
+      for (int u = tid; u < ng * units; u += kThr) {
+        const int g = u / units;
+        const int e0 = (u - g * units) * 8;
+        int mu = e0 / nsig, sp = e0 - mu * nsig;
+        uint32_t w0[4], w1[4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          uint16_t a0, a1, b0, b1;
+          const float va = mu < T.cv ? tile[(g * nsig + sp) * kTilePitch + mu] * out_scale : 0.f;
+          if (++sp == nsig) {
+            sp = 0;
+            ++mu;
+          }
+          const float vb = mu < T.cv ? tile[(g * nsig + sp) * kTilePitch + mu] * out_scale : 0.f;
+          if (++sp == nsig) {
+            sp = 0;
+            ++mu;
+          }
+          pack_slices(va, f, a0, a1);
+          pack_slices(vb, f, b0, b1);
+          w0[k / 2] = static_cast<uint32_t>(a0) | (static_cast<uint32_t>(b0) << 16);
+          w1[k / 2] = static_cast<uint32_t>(a1) | (static_cast<uint32_t>(b1) << 16);
+        }
+        const long long dst = static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk + tk.seg +
+                              static_cast<long long>(mu0) * nsig + e0;
+        *reinterpret_cast<uint4*>(out + dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(out + slice_elems + dst) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+      }
+      // norms: rectangles (RI atom of the rows) x (mu-atom of the columns)
+      const int pf = atom_of_ri[tk.p0 + pw0], pl = atom_of_ri[tk.p0 + pw0 + ng - 1];
+      const int mf = atom_of_ao[mu_base + mu0], ml = atom_of_ao[mu_base + mu0 + T.cv - 1];
+      const int np = pl - pf + 1;
+      for (int k = ep.warp; k < (ml - mf + 1) * np; k += kEpiWarps) {
+        const int m = mf + k / np, pa = pf + k % np;
+        const int g0 = max(0, ri_off[pa] - tk.p0 - pw0), g1 = min(ng, ri_off[pa + 1] - tk.p0 - pw0);
+        const int cc0 = max(0, ao_off[m] - mu_base - mu0), cc1 = min(T.cv, ao_off[m + 1] - mu_base - mu0);
+        rect_norm(tile, g0 * nsig, g1 * nsig, cc0, cc1, lane, norm2,
+                  (tk.s_local * nmc + (m - m_base)) * npa + (pa - pa0));
+      }
+    } else {
+      const int nm = n_ao[tk.owner];            // mu' per pw run
+      const int ng = T.cv / nm;
+      const int pw0 = T.rb / nm;
+      const int sf = atom_of_ao[row_ao0 + T.ra], sl = atom_of_ao[row_ao0 + T.ra + T.rv - 1];
+      const int ns = sl - sf + 1;
+      // one region (owner s, pw) per warp in turn: write and norm together
+      for (int k = ep.warp; k < ns * ng; k += kEpiWarps) {
+        const int s = sf + k / ng, g = k % ng;
+        const int nsg = n_ao[s];
+        const int r0 = ao_off[s] - row_ao0 - T.ra;   // staged row of sigma' = 0
+        const long long dst = static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk +
+                              rowbase[ao_off[s] - row_ao0] + static_cast<long long>(tk.aom) * nsg;
+        const int len = nm * nsg;
+        float ss = 0.f;
+        for (int e = lane; e < len; e += 32) {
+          const int mp = e / nsg, sp = e - mp * nsg;
+          const float v = tile[(r0 + sp) * kTilePitch + g * nm + mp];
+          ss += v * v;
+          uint16_t h0, h1;
+          pack_slices(v * out_scale, f, h0, h1);
+          out[dst + e] = h0;
+          out[slice_elems + dst + e] = h1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const int pa = atom_of_ri[tk.p0 + pw0 + g];
+        if (lane == 0 && ss != 0.f)
+          atomicAdd(norm2 + ((s - s0b) * nmc + (tk.owner - m_base)) * npa + (pa - pa0), ss);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(ep.freed);
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
@@ -540,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_tc_persistent(const __grid_constant__ CUtensorMap map_a,
                     const __grid_constant__ CUtensorMap map_b, const Job job, Cadence cad,
                     int* __restrict__ err_flag) {
-  using L = Smem<S>;
+  using L = Smem<S, Job>;
   constexpr int kStages = L::kStages;
   constexpr int kSub = kStageK / kMmaK;  // MMA steps per K step
   extern __shared__ uint8_t smem_raw[];
@@ -557,7 +773,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* small_empty = small_full + 1;
   uint64_t* drain = small_empty + 1;
   uint64_t* never = drain + 1;  // arrived at by nothing (stall test hook)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  uint64_t* tile_staged = never + 1;  // tile-staging jobs: every epilogue warp staged its part
+  uint64_t* tile_freed = tile_staged + 1;  // ... and finished writing the tile out
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_freed + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
 
@@ -574,6 +792,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(small_empty, kEpiWarps);
     mbar_init(drain, 1);
     mbar_init(never, 1);
+    mbar_init(tile_staged, kEpiWarps);
+    mbar_init(tile_freed, kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -726,6 +946,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0);
     float acc[kEpiCols];
     int chunk = 0, schunk = 0;
+    EpiCtx ep{staging, tile_staged, tile_freed, abort_flag, warp - 2, 0};
+    (void)ep;
     // test hook: a dependency that is never satisfied; the bounded wait
     // gives up and the kernel reports a time-out instead of hanging
     bool ok = cad.stall ? mbar_wait(never, 0, abort_flag) : true;
@@ -760,14 +982,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++schunk;
           cin = 0;
         }
-        if (Job::kPeriodic && (c + 1) % cad.write_every == 0 && c + 1 < nch) {
-          job.write(acc, T, quad, lane, c0, stg);
+        if constexpr (Job::kPeriodic) {
+          if ((c + 1) % cad.write_every == 0 && c + 1 < nch) {
+            job.write(acc, T, quad, lane, c0, stg);
 #pragma unroll
-          for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
+            for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
+          }
         }
       }
       if (!ok) break;
-      if (nch > 0) job.write(acc, T, quad, lane, c0, stg);
+      if (nch > 0) {
+        if constexpr (Job::kTileStaging) {
+          ok = job.write_staged(acc, T, quad, lane, c0, ep);
+          ++ep.tile_no;
+          if (!ok) break;
+        } else {
+          job.write(acc, T, quad, lane, c0, stg);
+        }
+      }
     }
     if (!ok) {
       *abort_flag = 1;
@@ -1182,7 +1414,7 @@ template <int S, class Job, bool F16>
 int launch_persistent_t(const CUtensorMap& ma, const CUtensorMap& mb, const Job& job, tc::Cadence cad,
                         int* err_flag, cudaStream_t st) {
   if (job.n_tiles == 0) return 0;
-  constexpr int smem = tc::Smem<S>::kTotal;
+  constexpr int smem = tc::Smem<S, Job>::kTotal;
   // the shared-memory opt-in is a per-device attribute of the kernel; setting
   // it twice (two threads racing on a first launch) is harmless
   static std::atomic<unsigned long long> attr_set{0};
@@ -1246,8 +1478,9 @@ int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, c
                   const int* tile_list, int n_tiles, const int* tasks, const int* counts, int max_slab,
                   const long long* slab_k0, const int* slab_len, int P0, int prow, int nri, int Q0,
                   int qrow, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st) {
+  (void)qrow;
   tc::ChiJob job{tile_list, n_tiles, nullptr, nullptr, tasks, counts, max_slab, slab_k0, slab_len, nqt,
-                 P0, prow, nri, Q0, qrow, chi, out_scale, nullptr};
+                 P0, prow, nri, nri - Q0, chi + Q0, out_scale, nullptr};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
@@ -1257,8 +1490,9 @@ int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap&
                         const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
                         int P0, int prow, int nri, int Q0, int qrow, int nqt, double* chi, int flush_k,
                         int* err_flag, cudaStream_t st) {
+  (void)qrow;
   tc::ChiJob job{unit_tile, n_units, unit_first, unit_count, tasks, counts, max_slab, slab_k0, slab_len,
-                 nqt, P0, prow, nri, Q0, qrow, chi, out_scale, n_units_dev};
+                 nqt, P0, prow, nri, nri - Q0, chi + Q0, out_scale, n_units_dev};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
@@ -1275,6 +1509,22 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
   // mode 0: the panel rows are the A operand
   if (mode == 0) return launch_persistent(slices, f16, mp, mg, job, flush_k, err_flag, st);
   return launch_persistent(slices, f16, mg, mp, job, flush_k, err_flag, st);
+}
+
+int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtensorMap& mg,
+                           const CUtensorMap& mp, const int4* tiles, int n_tiles,
+                           const PanelTaskTC* tasks, int mode, void* out, long long slice_elems,
+                           long long ldk, int P0b, int Lc, int row_ao0, int s0b,
+                           const long long* rowbase, float* norm2, const int* atom_of_ri,
+                           const int* atom_of_ao, const int* ao_off, const int* ri_off,
+                           const int* n_ao, int npa, int pa0, int mu_base, int m_base, int nmc,
+                           int flush_k, int* err_flag, cudaStream_t st) {
+  tc::PanelStagedJob job{tiles, n_tiles, tasks, mode, static_cast<uint16_t*>(out), slice_elems, ldk,
+                         P0b, Lc, row_ao0, s0b, rowbase, norm2, atom_of_ri, atom_of_ao, ao_off, ri_off,
+                         n_ao, npa, pa0, mu_base, m_base, nmc, f16, unscale, out_scale};
+  // mode 0: the panel rows are the A operand
+  if (mode == 0) return launch_persistent(2, f16, mp, mg, job, flush_k, err_flag, st);
+  return launch_persistent(2, f16, mg, mp, job, flush_k, err_flag, st);
 }
 
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,

@@ -83,6 +83,20 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
                     const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
                     int pa0, int mu_base, int m_base, int nmc, int flush_k, int* err_flag,
                     cudaStream_t st);
+// Steps A/B with the staged epilogue (two slices; PanelStagedJob in k_tc.cu).
+// Tile entries (task, A row offset, B row offset, rows_valid << 16 |
+// cols_valid): mode 0 A = owner panel rows from a pw boundary, B = G^occ rows
+// of the chunk; mode 1 A = batch rows of whole owner atoms (<= 128), B =
+// panel rows from a pw boundary.  Lc: chunk segment length (mode 0);
+// row_ao0, s0b: first AO and first owner atom of the batch (mode 1).
+int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtensorMap& mg,
+                           const CUtensorMap& mp, const int4* tiles, int n_tiles,
+                           const PanelTaskTC* tasks, int mode, void* out, long long slice_elems,
+                           long long ldk, int P0b, int Lc, int row_ao0, int s0b,
+                           const long long* rowbase, float* norm2, const int* atom_of_ri,
+                           const int* atom_of_ao, const int* ao_off, const int* ri_off,
+                           const int* n_ao, int npa, int pa0, int mu_base, int m_base, int nmc,
+                           int flush_k, int* err_flag, cudaStream_t st);
 // Zero the part of the step-B operand Y that step B does not write: for each
 // Y row (RI function Q0 + ql, ql < qrow) and batch atom s, the chunk-local mu
 // (chunk atoms [m0, m1), segment Lc functions) outside the owner atoms

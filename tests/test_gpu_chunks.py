@@ -94,3 +94,18 @@ def test_filtered_chunks_are_skipped(lib):
     got, st = _run(lib, case, "fp16x3", thr, {"mu_chunk_atoms": 6, "batch_atoms": 6})
     _check(got, ref, 1e-6)
     assert st["batches_skipped"] > 0
+
+
+@pytest.mark.parametrize("name", ["benzene", "ribbon28"])
+@pytest.mark.parametrize("chunk", [0, 7])
+def test_staged_epilogue_writes_the_same_operands(lib, name, chunk):
+    """The staged step-A/B epilogue (whole runs of X and Y from a tile staged
+    in shared memory) computes every operand element in the same order as
+    the per-element one: with whole-tile step-C units (a fixed summation
+    order) and nothing filtered, chi is bitwise the same."""
+    case = make_case(name, n_tau=2)
+    opts = {"c_split_k": 0, "mu_chunk_atoms": chunk}
+    a, _ = _run(lib, case, "fp16x3", 0.0, dict(opts, panel_staged=1))
+    b, _ = _run(lib, case, "fp16x3", 0.0, dict(opts, panel_staged=0))
+    assert np.array_equal(a, b)
+    _check(a, oc.chi_dense(case, thr=0.0), 1e-6)

@@ -99,6 +99,16 @@ def test_fp64_full_size_sampled_blocks(setup, j):
         ctx.load_case(case)
         chi = ctx.chi_tau(case.thr, "fp64", j, 1)[0]
         got = _blocks(chi, ri, _pairs(sets[j]))
+        st = ctx.stats()
     rel, el = _errors(got, _reference(bo, refs, j, sets[j]))
     print(f"fp64 tau[{j}]: rel Frobenius {rel:.2e}, element {el:.2e}")
     assert rel <= 1e-10 and el <= 1e-10
+    # the useful-flop count equals the oracle's own count where one was taken
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "flops_ribbon298.json")
+    golden = json.load(open(path))["per_tau"].get(str(j))
+    if golden is not None:
+        for k in ("flops_a", "flops_b", "flops_c"):
+            assert st[k] == pytest.approx(golden[k], rel=1e-12), (k, st[k], golden[k])

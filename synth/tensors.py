@@ -100,14 +100,27 @@ def make_three_center(sysm: System, thr: float, seed: int) -> ThreeCenter:
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     total = int(offsets[-1])
     data = normal_stream(seed, STREAM_3C, 0, total)
-    # scale each block, symmetrise A == B blocks
-    per_elem = np.repeat(scales, sizes)
-    data *= per_elem
+    # scale each block (runs of blocks of at most 2^26 elements at a time, so
+    # that no second array of the tensor's size is needed)
+    b0 = 0
+    step = 1 << 26
+    while b0 < len(sizes):
+        b1 = int(np.searchsorted(offsets, offsets[b0] + step, side="right")) - 1
+        b1 = min(max(b1, b0 + 1), len(sizes))
+        data[offsets[b0]:offsets[b1]] *= np.repeat(scales[b0:b1], sizes[b0:b1])
+        b0 = b1
+    # symmetrise A == B blocks, (X + X^T) / 2 in the primary indices, grouped by
+    # block shape
     diag = np.nonzero(blocks[:, 0] == blocks[:, 1])[0]
-    for i in diag:
-        a, _, p = blocks[i]
-        blk = data[offsets[i]:offsets[i + 1]].reshape(nao[a], nao[a], nri[p])
-        blk[...] = 0.5 * (blk + blk.transpose(1, 0, 2))
+    shapes = np.stack([nao[blocks[diag, 0]], nri[blocks[diag, 2]]], axis=1)
+    for na, npp in np.unique(shapes, axis=0):
+        ids = diag[(shapes[:, 0] == na) & (shapes[:, 1] == npp)]
+        sz = int(na * na * npp)
+        for c0 in range(0, len(ids), 4096):
+            sel = ids[c0:c0 + 4096]
+            pos = offsets[sel][:, None] + np.arange(sz)[None, :]
+            blk = data[pos].reshape(-1, na, na, npp)
+            data[pos] = (0.5 * (blk + blk.transpose(0, 2, 1, 3))).reshape(len(sel), sz)
     return ThreeCenter(blocks, offsets, data)
 
 
@@ -160,6 +173,8 @@ CASES = {
     "ribbon28": (lambda: armchair_ribbon(2.5), 4, 1e-9, 20210425),
     "ribbon60": (lambda: armchair_ribbon(5), 6, 1e-9, 20210426),
     "ribbon120": (lambda: armchair_ribbon(10), 6, 1e-9, 20210427),
+    # 144.5 cells: 1156 C + 576 H = 1732 atoms, 17 908 AO / 41 592 RI
+    "ribbon1734": (lambda: armchair_ribbon(144.5), 30, 1e-9, 20210423),
     "chain_HH": (lambda: tiny_chain("HH", 1.0), 3, 0.0, 6),
     "chain_CH": (lambda: tiny_chain("CH"), 3, 0.0, 7),
     "chain_HCH": (lambda: tiny_chain("HCH"), 3, 0.0, 8),

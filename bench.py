@@ -336,6 +336,32 @@ def _train_screen(Context, device, thr, precision):
                             "margin": margin, "trained_on": "benzene, ribbon28, ribbon60 task logs"}
 
 
+def _per_tau_parity(case, run_tau, out, ri, prec, taus):
+    """Error of the timed form at the given tau points, each on the diagonal
+    chi block of one RI atom (atom j of a seeded permutation) that the FP64
+    block oracle computes from its own M and N slices."""
+    import numpy as np
+    import torch
+
+    from oracle import chi as oc
+
+    bo = oc.BlockOracle(case)
+    perm = np.random.default_rng(20210420).permutation(case.system.n_atoms)
+    per_tau, oracle_blocks = [], {}
+    for j in taus:
+        a = int(perm[j])
+        ref = bo.block(j, a, a, {})
+        oracle_blocks[j] = (a, ref)
+        run_tau(j)
+        torch.cuda.synchronize()
+        rel, el = _block_errors(_diag_blocks(out[0], ri, [a]), [ref])
+        per_tau.append({"tau_index": j, "atom": a, "rel_frobenius": rel, "rel_element": el})
+    res = {"form": prec, "reference": "numpy FP64 block oracle", "per_tau": per_tau,
+           "max_rel_frobenius": max(p["rel_frobenius"] for p in per_tau),
+           "max_rel_element": max(p["rel_element"] for p in per_tau)}
+    return res, oracle_blocks
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -363,6 +389,8 @@ def run_ours(args):
     ctx = Context(local, stream)
     if args.batch_atoms > 0:
         ctx.set_option("batch_atoms", args.batch_atoms)
+    if args.batch_bytes > 0:
+        ctx.set_option("batch_bytes", args.batch_bytes)
     ctx.load_case(case)
     nri = ctx.nri
     out = torch.empty((1, nri, nri), dtype=torch.float64, device=f"cuda:{local}")
@@ -374,6 +402,18 @@ def run_ours(args):
             ctx.chi_tau(case.thr, precision, j, 1, out=out, screening=screening)
         return ctx.stats()
 
+    # schedule search of the tensor-core route (before the warm-up; the
+    # context keeps the chosen knobs)
+    tune = None
+    if args.autotune and prec in SPLIT_FORMS:
+        from paper_2104_09857_gb300 import _lib as _l
+
+        trials = _l.gw_autotune(ctx.ctx, n_tau // 2, case.thr, _l.PRECISIONS[prec])
+        best = min(trials, key=lambda t: t["ms"])
+        tune = {"tau_index": n_tau // 2, "trials": trials,
+                "chosen": {k: best[k] for k in ("panel_staged", "c_split_k", "batch_bytes",
+                                                "mu_chunk_atoms")},
+                "start_ms": trials[0]["ms"], "chosen_ms": best["ms"]}
     # warm-up (W steps on the first tau points of this rank's cycle)
     for w in range(args.warmup):
         step(tau_index(w, world, rank, n_tau), prec)
@@ -443,6 +483,8 @@ def run_ours(args):
     }
     if alu:
         result["alu_peaks"] = alu
+    if tune:
+        result["autotune"] = tune
 
     if rank == 0 and world == 1 and args.workload == WORKLOAD:
         from oracle import chi as oc
@@ -484,21 +526,8 @@ def run_ours(args):
         forms["useful_flops_oracle"] = flops_oracle
         result["forms"] = forms
         # per-tau parity of the timed form: one diagonal block per tau point
-        # (atom a_j of a seeded permutation), oracle M and N slices each
-        bo = oc.BlockOracle(case)
-        perm = np.random.default_rng(20210420).permutation(case.system.n_atoms)
-        per_tau, oracle_blocks = [], {}
-        for j in range(min(args.parity_taus, n_tau)):
-            a = int(perm[j])
-            ref = bo.block(j, a, a, {})
-            oracle_blocks[j] = (a, ref)
-            step(j, prec)
-            torch.cuda.synchronize()
-            rel, el = _block_errors(_diag_blocks(out[0], ri, [a]), [ref])
-            per_tau.append({"tau_index": j, "atom": a, "rel_frobenius": rel, "rel_element": el})
-        result["parity"] = {"form": prec, "reference": "numpy FP64 block oracle", "per_tau": per_tau,
-                            "max_rel_frobenius": max(p["rel_frobenius"] for p in per_tau),
-                            "max_rel_element": max(p["rel_element"] for p in per_tau)}
+        result["parity"], oracle_blocks = _per_tau_parity(
+            case, lambda j: step(j, prec), out, ri, prec, list(range(min(args.parity_taus, n_tau))))
         # learned screening at the bench threshold: time, skipped tasks,
         # per-tau error on the same oracle blocks
         if args.learned:
@@ -562,6 +591,12 @@ def run_ours(args):
                              "d2h_bytes_per_step": int(nri * nri * 8),
                              "ms_per_step": t_e * 1e3 / args.e2e_steps}
         result["setup"] = {"generate_s": t_gen}
+    elif rank == 0 and world == 1 and args.parity_taus > 0:
+        # other workloads: sampled parity at tau points spread over the grid
+        ri = np.concatenate([[0], np.cumsum(case.system.n_ri)])
+        taus = sorted({int(round(x)) for x in np.linspace(0, n_tau - 1, min(args.parity_taus, n_tau))})
+        result["parity"], _ = _per_tau_parity(case, lambda j: step(j, prec), out, ri, prec, taus)
+        result["setup"] = {"generate_s": t_gen}
     ctx.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -593,6 +628,10 @@ def main():
                     help="synthetic case (smaller ones serve profiling); the bench line is %(default)s")
     ap.add_argument("--batch-atoms", type=int, default=0,
                     help="upper limit on sigma-atoms per operand batch (0: byte budget only)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="search the tensor-core schedule (gw_autotune) before the warm-up")
+    ap.add_argument("--batch-bytes", type=float, default=0,
+                    help="device bytes for one batch's X and Y operands (0: the library default)")
     args = ap.parse_args()
     if args.peaks:
         import __graft_entry__ as g

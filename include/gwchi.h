@@ -384,6 +384,31 @@ int gw_evgw(gw_ctx* ctx, const double* V, int n_omega, const double* omega, cons
             const double* vxc, double thr, int precision, int max_cycles, double tol,
             double* qp_out, int* cycles_out);
 
+/* Schedule search of the tensor-core chi route (no counterpart in the paper;
+ * a tuner for this library's own schedule).  Searches, by coordinate descent
+ * from the context's current options, the knobs that change only the order
+ * and grouping of the work -- "panel_staged", "c_split_k", "batch_bytes"
+ * (0.5x, 1x, 1.5x of the current budget, where device memory allows) and
+ * "mu_chunk_atoms" (automatic, n_atoms/4, n_atoms/2) -- timing each candidate
+ * as the device time of gw_chi_tau on tau point tau_index (one untimed call
+ * first), and leaves the fastest value of each knob set in the context.
+ * "flush_k" is not searched: it sets the accuracy of the FP32 accumulation.
+ * trials[0 .. min(*n_trials, max_trials)) log every timing (the first is the
+ * starting point).  Needs the inputs set (GW_ERR_ORDER); precision must be a
+ * tensor-core form (GW_ERR_UNSUPPORTED).  Allocates one n_RI^2 FP64 chi
+ * buffer for the duration of the call. */
+typedef struct gw_tune_trial {
+  char knob[32];     /* knob varied in this trial ("start" for the first)     */
+  double value;      /* its value                                            */
+  double ms;         /* device time of one gw_chi_tau(tau_index) call        */
+  int panel_staged;  /* the full setting timed                               */
+  int c_split_k;
+  double batch_bytes;
+  int mu_chunk_atoms;
+} gw_tune_trial;
+int gw_autotune(gw_ctx* ctx, int tau_index, double thr, int precision, gw_tune_trial* trials,
+                int max_trials, int* n_trials);
+
 /* Counters and timings of the last gw_chi_tau call. */
 int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
 

@@ -74,6 +74,23 @@ class gw_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gw_tune_trial(ctypes.Structure):
+    _fields_ = [
+        ("knob", ctypes.c_char * 32),
+        ("value", ctypes.c_double),
+        ("ms", ctypes.c_double),
+        ("panel_staged", ctypes.c_int),
+        ("c_split_k", ctypes.c_int),
+        ("batch_bytes", ctypes.c_double),
+        ("mu_chunk_atoms", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["knob"] = self.knob.decode()
+        return d
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _LL = ctypes.c_longlong
@@ -108,6 +125,7 @@ SIGNATURES = [
     ("gw_sigma_ao_tau", _I, [_P, _P, _I, _D, _P, _I]),
     ("gw_evgw", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I, _D, _P,
                      ctypes.POINTER(_I)]),
+    ("gw_autotune", _I, [_P, _I, _D, _I, ctypes.POINTER(gw_tune_trial), _I, ctypes.POINTER(_I)]),
 ]
 
 MLP_FEATURES = 8
@@ -362,6 +380,17 @@ def gw_mlp_predict(ctx: int, feat) -> np.ndarray:
     pred = np.zeros(feat.shape[0], dtype=np.float32)
     _check(ctx, lib().gw_mlp_predict(ctx, _ptr(feat), feat.shape[0], _ptr(pred)))
     return pred
+
+
+def gw_autotune(ctx: int, tau_index: int, thr: float, precision: int, max_trials: int = 64) -> list:
+    """Schedule search of the tensor-core route; returns the logged trials
+    (dicts), the first being the starting point; the context keeps the
+    fastest setting of each knob."""
+    arr = (gw_tune_trial * max_trials)()
+    n = ctypes.c_int(0)
+    _check(ctx, lib().gw_autotune(ctx, int(tau_index), float(thr), int(precision), arr, max_trials,
+                                  ctypes.byref(n)))
+    return [arr[i].as_dict() for i in range(min(n.value, max_trials))]
 
 
 def gw_get_stats(ctx: int) -> dict:

@@ -109,3 +109,22 @@ def test_staged_epilogue_writes_the_same_operands(lib, name, chunk):
     b, _ = _run(lib, case, "fp16x3", 0.0, dict(opts, panel_staged=0))
     assert np.array_equal(a, b)
     _check(a, oc.chi_dense(case, thr=0.0), 1e-6)
+
+
+def test_autotune_keeps_the_fastest_schedule_and_the_result(lib):
+    """The schedule search logs every timing, leaves the context on a
+    setting at least as fast as where it started, and chi computed with the
+    chosen schedule still matches the oracle."""
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("ribbon28", n_tau=2)
+    ref = oc.chi_dense(case)
+    with lib.Context(0) as ctx:
+        ctx.load_case(case)
+        trials = _lib.gw_autotune(ctx.ctx, 1, case.thr, _lib.GW_FP16X3)
+        got = ctx.chi_tau(case.thr, "fp16x3").cpu().numpy()
+    assert trials[0]["knob"] == "start" and len(trials) >= 6
+    best = min(t["ms"] for t in trials)
+    assert best <= trials[0]["ms"]
+    assert all(t["ms"] > 0 for t in trials)
+    _check(got, ref, 1e-6)

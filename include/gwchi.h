@@ -288,6 +288,27 @@ int gw_sigma_ao_tau(gw_ctx* ctx, const double* W_tau, int w_on_device, double th
 int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const int* orbitals, int n_orb,
                double thr, int precision, double* sx_out);
 
+/* Batched form of gw_sigma_tau for many molecules (the uneven molecule set of
+ * the batched self-energy workload): Eq. 10 for the orbitals orbitals[i][0 ..
+ * n_orb[i]) of the molecule held by context ctxs[i] (basis, tensor and
+ * Green's functions set; every context on the same device, all with the same
+ * number of tau points).  W_tau[i]: [n_tau][n_ri_i][n_ri_i] FP64, host (or
+ * device when w_on_device); sigma_out[i]: [n_orb[i]][n_tau][2] host, the
+ * layout of gw_sigma_tau.  Split forms (GW_BF16X3, GW_BF16X6, GW_FP16X3):
+ * per tau point, each of the two products of Eq. 10 -- Y = B^n W and
+ * Z = Y B^nT, every (molecule, orbital) pair -- is one persistent
+ * tensor-core launch over all pairs' tiles, and the traces with G^occ and
+ * G^virt one more launch; B^n is formed once per molecule from its FP64
+ * panels, which are then released (one molecule's panels are resident at a
+ * time).  GW_FP64 runs gw_sigma_tau's FP64 route molecule by molecule.
+ * Runs on the stream of ctxs[0]; messages go to ctxs[0]'s gw_last_error.
+ * Errors: GW_ERR_INVALID_ARG (null or mismatched arguments, devices or tau
+ * counts, orbital index), GW_ERR_ORDER (a context without inputs),
+ * GW_ERR_UNSUPPORTED (precision), GW_ERR_OOM, GW_ERR_CUDA, GW_ERR_TIMEOUT. */
+int gw_sigma_tau_batch(gw_ctx* const* ctxs, int n_mol, const double* const* W_tau, int w_on_device,
+                       const int* const* orbitals, const int* n_orb, double thr, int precision,
+                       double* const* sigma_out);
+
 /* G0W0 quasiparticle energies, Eq. 12, FP64 on the device, from the diagonal
  * self-energy on imaginary time (the output layout of gw_sigma_tau):
  *   Sigma^c_n(i omega_k) = sum_j [gamma_kj / 2 (S+_j + S-_j) - i s_kj (S+_j - S-_j)]

@@ -126,6 +126,7 @@ SIGNATURES = [
     ("gw_evgw", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I, _D, _P,
                      ctypes.POINTER(_I)]),
     ("gw_autotune", _I, [_P, _I, _D, _I, ctypes.POINTER(gw_tune_trial), _I, ctypes.POINTER(_I)]),
+    ("gw_sigma_tau_batch", _I, [_P, _I, _P, _I, _P, _P, _D, _I, _P]),
 ]
 
 MLP_FEATURES = 8
@@ -380,6 +381,24 @@ def gw_mlp_predict(ctx: int, feat) -> np.ndarray:
     pred = np.zeros(feat.shape[0], dtype=np.float32)
     _check(ctx, lib().gw_mlp_predict(ctx, _ptr(feat), feat.shape[0], _ptr(pred)))
     return pred
+
+
+def gw_sigma_tau_batch(ctxs: list, w_taus: list, orbitals: list, thr: float, precision: int) -> list:
+    """Diagonal Sigma^c of several molecules (one context each) in one call:
+    w_taus[i] host arrays [n_tau, n_RI_i, n_RI_i]; returns numpy arrays
+    [n_orb_i, n_tau, 2] per molecule."""
+    n = len(ctxs)
+    ws = [np.ascontiguousarray(w, dtype=np.float64) for w in w_taus]
+    orbs = [np.ascontiguousarray(o, dtype=np.int32) for o in orbitals]
+    n_tau = ws[0].shape[0]
+    outs = [np.zeros((o.size, n_tau, 2)) for o in orbs]
+    c_ctx = (_P * n)(*ctxs)
+    c_w = (_P * n)(*[w.ctypes.data for w in ws])
+    c_o = (_P * n)(*[o.ctypes.data for o in orbs])
+    c_n = (ctypes.c_int * n)(*[o.size for o in orbs])
+    c_out = (_P * n)(*[o.ctypes.data for o in outs])
+    _check(ctxs[0], lib().gw_sigma_tau_batch(c_ctx, n, c_w, 0, c_o, c_n, float(thr), int(precision), c_out))
+    return outs
 
 
 def gw_autotune(ctx: int, tau_index: int, thr: float, precision: int, max_trials: int = 64) -> list:

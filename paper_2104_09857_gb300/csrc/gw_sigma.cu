@@ -363,3 +363,403 @@ extern "C" int gw_sigma_x(gw_ctx* ctx, const double* V, int v_on_device, const i
   for (int a = 0; a < n_orb; ++a) sx_out[a] = tmp[(size_t)a * 2];
   return GW_OK;
 }
+
+// ===========================================================================
+// batched self-energy: many molecules, one grouped launch per product
+// ===========================================================================
+namespace gw {
+namespace sigma {
+
+// partial[(p * kDotBlocks + b) * 2 + 0..1] = block b's part of
+// (sum G^occ * Z_p, sum G^virt * Z_p) over problem p's n elements
+struct DotDesc {
+  long long g_off, z_off, n;
+};
+__global__ void k_dot2_group(const double* __restrict__ go, const double* __restrict__ gv,
+                             const double* __restrict__ z, const DotDesc* __restrict__ desc,
+                             double* __restrict__ partial) {
+  __shared__ double s0[256], s1[256];
+  const DotDesc d = desc[blockIdx.y];
+  double a = 0.0, b = 0.0;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < d.n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const double zz = z[d.z_off + i];
+    a = fma(go[d.g_off + i], zz, a);
+    b = fma(gv[d.g_off + i], zz, b);
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s0[threadIdx.x] += s0[threadIdx.x + o];
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* o = partial + (static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x) * 2;
+    o[0] = s0[0];
+    o[1] = s1[0];
+  }
+}
+
+}  // namespace sigma
+}  // namespace gw
+
+namespace {
+
+#define SB_TRY(call)                                                                         \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      c0->err = std::string("gw_sigma_tau_batch: ") + #call + ": " + cudaGetErrorString(e_); \
+      return e_ == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA;                     \
+    }                                                                                        \
+  } while (0)
+
+struct Prob {
+  int mol, a, nao, nri;
+  long long rowB;  // first slice row of B_p (and of Y_p)
+  long long offY, offZ;
+};
+
+int sigma_batch_mixed(gw_ctx* const* ctxs, int n_mol, const double* const* W_tau, int w_on_device,
+                      const int* const* orbitals, const int* n_orb, double thr, int precision,
+                      double* const* sigma_out) {
+  gw_ctx* c0 = ctxs[0];
+  cudaStream_t st = c0->stream;
+  const int slices = precision == GW_BF16X6 ? 3 : 2;
+  const int f16 = precision == GW_FP16X3;
+  const int n_tau = (int)c0->tau.size();
+  const int tile = gw::tc_tile_rows();
+  // problems (molecule, orbital) and the buffers' layout
+  std::vector<Prob> pr;
+  std::vector<long long> offB64(n_mol), offW(n_mol), offG(n_mol), offWrow(n_mol);
+  long long nB64 = 0, nW = 0, nG = 0, rowsB = 0, rowsW = 0, nY = 0, nZ = 0;
+  int kmax = 64, max_nao = 1, max_nri = 1, max_occ = 1, max_virt = 1;
+  for (int i = 0; i < n_mol; ++i) {
+    const gw_ctx* c = ctxs[i];
+    offB64[i] = nB64;
+    offW[i] = nW;
+    offG[i] = nG;
+    offWrow[i] = rowsW;
+    nB64 += (long long)n_orb[i] * c->nao * c->nri;
+    nW += (long long)c->nri * c->nri;
+    nG += (long long)c->nao * c->nao;
+    rowsW += c->nri;
+    kmax = std::max(kmax, (c->nri + 63) / 64 * 64);
+    max_nao = std::max(max_nao, c->nao);
+    max_nri = std::max(max_nri, c->nri);
+    max_occ = std::max(max_occ, c->n_occ);
+    max_virt = std::max(max_virt, c->nao - c->n_occ);
+    for (int a = 0; a < n_orb[i]; ++a) {
+      Prob p{i, a, c->nao, c->nri, rowsB, nY, nZ};
+      rowsB += c->nao;
+      nY += (long long)c->nao * c->nri;
+      nZ += (long long)c->nao * c->nao;
+      pr.push_back(p);
+    }
+  }
+  const int np = (int)pr.size();
+  DevBuf b_bn, b_csel, b_bs, b_ws, b_ys, b_w64, b_y64, b_z64, b_go, b_gv, b_cso, b_csv, b_fl, b_mx,
+      b_sd, b_t1, b_t2, b_dd, b_part, b_err, b_pd, b_own;
+  SB_TRY(cudaMalloc(&b_bn.p, std::max<long long>(nB64, 1) * 8));
+  SB_TRY(cudaMemsetAsync(b_bn.p, 0, std::max<long long>(nB64, 1) * 8, st));
+  double* bn = (double*)b_bn.p;
+  // B^n of every molecule from its FP64 panels (built and released one
+  // molecule at a time, so that one pool is resident at once)
+  for (int i = 0; i < n_mol; ++i) {
+    gw_ctx* c = ctxs[i];
+    int rc = gw::build_panels_for(c, thr);
+    if (rc) {
+      c0->err = "gw_sigma_tau_batch: molecule " + std::to_string(i) + ": " + c->err;
+      return rc;
+    }
+    DevBuf csel;
+    SB_TRY(cudaMalloc(&csel.p, (size_t)c->nao * n_orb[i] * 8));
+    for (int a = 0; a < n_orb[i]; ++a)
+      SB_TRY(cudaMemcpy2DAsync((double*)csel.p + a, n_orb[i] * 8, c->d_C + orbitals[i][a], c->nao * 8, 8,
+                               c->nao, cudaMemcpyDeviceToDevice, st));
+    std::vector<int> owners;
+    int maxN = 0;
+    for (int s = 0; s < c->n_at; ++s)
+      if (c->panels[s].K > 0) {
+        owners.push_back(s);
+        maxN = std::max(maxN, c->panels[s].npw * c->panels[s].nsig);
+      }
+    DevBuf pd, own;
+    SB_TRY(cudaMalloc(&pd.p, c->panels.size() * sizeof(gw::PanelDesc)));
+    SB_TRY(cudaMemcpyAsync(pd.p, c->panels.data(), c->panels.size() * sizeof(gw::PanelDesc),
+                           cudaMemcpyHostToDevice, st));
+    SB_TRY(cudaMalloc(&own.p, std::max<size_t>(owners.size(), 1) * sizeof(int)));
+    if (!owners.empty()) {
+      SB_TRY(cudaMemcpyAsync(own.p, owners.data(), owners.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      dim3 g((maxN + 127) / 128, (unsigned)owners.size(), n_orb[i]);
+      gw::sigma::k_bn_panels<<<g, 128, 0, st>>>(c->d_panel64, (const gw::PanelDesc*)pd.p,
+                                                (const int*)own.p, c->d_lam, c->d_ao_off,
+                                                (const double*)csel.p, n_orb[i], c->nao, c->nri,
+                                                bn + offB64[i]);
+      SB_TRY(cudaGetLastError());
+    }
+    if (thr > 0.0) {
+      const long long nblk = (long long)n_orb[i] * c->n_at * c->n_at;
+      gw::sigma::k_bn_filter<<<(unsigned)((nblk + 7) / 8), 256, 0, st>>>(bn + offB64[i], n_orb[i], c->n_at,
+                                                                         c->nao, c->nri, c->d_ao_off,
+                                                                         c->d_ri_off, thr);
+      SB_TRY(cudaGetLastError());
+    }
+    SB_TRY(cudaStreamSynchronize(st));
+    // the pool is not needed again here: release it
+    cudaFree(c->d_panel64);
+    c->d_panel64 = nullptr;
+    c->panels_ok = false;
+    c->panels_thr = -1.0;
+    c->panel32_ok = false;
+  }
+  // slices of B (tau independent) with per-problem binary16 scales
+  std::vector<gw::SplitDesc> sd(np);
+  for (int p = 0; p < np; ++p) {
+    const Prob& q = pr[p];
+    sd[p] = gw::SplitDesc{offB64[q.mol] + (long long)q.a * q.nao * q.nri, q.rowB, q.nao, q.nri, q.nri, 0, 1.0};
+  }
+  SB_TRY(cudaMalloc(&b_sd.p, std::max(np, n_mol) * sizeof(gw::SplitDesc)));
+  SB_TRY(cudaMalloc(&b_mx.p, 2 * std::max(np, n_mol) * sizeof(double)));
+  std::vector<double> bmx(2 * np, 1.0);
+  if (f16) {
+    SB_TRY(cudaMemcpyAsync(b_sd.p, sd.data(), np * sizeof(gw::SplitDesc), cudaMemcpyHostToDevice, st));
+    gw::launch_absmax_group(bn, (const gw::SplitDesc*)b_sd.p, np, max_nao, (double*)b_mx.p, st);
+    SB_TRY(cudaGetLastError());
+    SB_TRY(cudaMemcpyAsync(bmx.data(), b_mx.p, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SB_TRY(cudaStreamSynchronize(st));
+  }
+  std::vector<double> s_b(np, 1.0);
+  for (int p = 0; p < np; ++p) {
+    if (f16) s_b[p] = gw::pow2_scale(bmx[2 * p]);
+    sd[p].scale = s_b[p];
+  }
+  SB_TRY(cudaMemcpyAsync(b_sd.p, sd.data(), np * sizeof(gw::SplitDesc), cudaMemcpyHostToDevice, st));
+  const long long bs_elems = std::max<long long>(rowsB, 1) * kmax;
+  SB_TRY(cudaMalloc(&b_bs.p, (size_t)slices * bs_elems * 2));
+  SB_TRY(cudaMalloc(&b_ys.p, (size_t)slices * bs_elems * 2));
+  gw::launch_split_group(bn, (const gw::SplitDesc*)b_sd.p, np, max_nao, kmax, slices, bs_elems, f16, b_bs.p, st);
+  SB_TRY(cudaGetLastError());
+  const long long ws_elems = std::max<long long>(rowsW, 1) * kmax;
+  SB_TRY(cudaMalloc(&b_ws.p, (size_t)slices * ws_elems * 2));
+  SB_TRY(cudaMalloc(&b_y64.p, std::max<long long>(nY, 1) * 8));
+  SB_TRY(cudaMalloc(&b_z64.p, std::max<long long>(nZ, 1) * 8));
+  SB_TRY(cudaMalloc(&b_go.p, std::max<long long>(nG, 1) * 8));
+  SB_TRY(cudaMalloc(&b_gv.p, std::max<long long>(nG, 1) * 8));
+  SB_TRY(cudaMalloc(&b_cso.p, (size_t)max_nao * max_occ * 8));
+  SB_TRY(cudaMalloc(&b_csv.p, (size_t)max_nao * max_virt * 8));
+  SB_TRY(cudaMalloc(&b_err.p, sizeof(int)));
+  SB_TRY(cudaMemsetAsync(b_err.p, 0, sizeof(int), st));
+  if (!w_on_device) SB_TRY(cudaMalloc(&b_w64.p, std::max<long long>(nW, 1) * 8));
+  int max_at = 1;
+  for (int i = 0; i < n_mol; ++i) max_at = std::max(max_at, ctxs[i]->n_at);
+  SB_TRY(cudaMalloc(&b_fl.p, (size_t)max_at * max_at));
+  CUtensorMap m_b, m_w, m_y;
+  if (gw::make_slice_map(&m_b, b_bs.p, kmax, std::max<long long>(rowsB, 1), slices, tile, f16) ||
+      gw::make_slice_map(&m_w, b_ws.p, kmax, std::max<long long>(rowsW, 1), slices, tile, f16) ||
+      gw::make_slice_map(&m_y, b_ys.p, kmax, std::max<long long>(rowsB, 1), slices, tile, f16)) {
+    c0->err = "gw_sigma_tau_batch: cuTensorMapEncodeTiled failed";
+    return GW_ERR_CUDA;
+  }
+  // dot descriptors and tiles of the two grouped products
+  std::vector<gw::sigma::DotDesc> dd(np);
+  for (int p = 0; p < np; ++p)
+    dd[p] = gw::sigma::DotDesc{offG[pr[p].mol], pr[p].offZ, (long long)pr[p].nao * pr[p].nao};
+  SB_TRY(cudaMalloc(&b_dd.p, np * sizeof(gw::sigma::DotDesc)));
+  SB_TRY(cudaMemcpyAsync(b_dd.p, dd.data(), np * sizeof(gw::sigma::DotDesc), cudaMemcpyHostToDevice, st));
+  SB_TRY(cudaMalloc(&b_part.p, (size_t)np * kDotBlocks * 2 * 8));
+  std::vector<double> part((size_t)np * kDotBlocks * 2);
+  std::vector<gw::GroupTile> t1, t2;
+  for (const Prob& q : pr) {
+    for (int mt = 0; mt * tile < q.nao; ++mt)
+      for (int nt = 0; nt * tile < q.nri; ++nt)
+        t1.push_back(gw::GroupTile{q.offY + (long long)mt * tile * q.nri + nt * tile, (int)(q.rowB + mt * tile),
+                                   (int)(offWrow[q.mol] + nt * tile), (q.nri + 63) / 64,
+                                   std::min(tile, q.nao - mt * tile), std::min(tile, q.nri - nt * tile), q.nri,
+                                   1.f, 0});
+    for (int mt = 0; mt * tile < q.nao; ++mt)
+      for (int nt = 0; nt * tile < q.nao; ++nt)
+        t2.push_back(gw::GroupTile{q.offZ + (long long)mt * tile * q.nao + nt * tile, (int)(q.rowB + mt * tile),
+                                   (int)(q.rowB + nt * tile), (q.nri + 63) / 64,
+                                   std::min(tile, q.nao - mt * tile), std::min(tile, q.nao - nt * tile), q.nao,
+                                   1.f, 0});
+  }
+  SB_TRY(cudaMalloc(&b_t1.p, std::max<size_t>(t1.size(), 1) * sizeof(gw::GroupTile)));
+  SB_TRY(cudaMalloc(&b_t2.p, std::max<size_t>(t2.size(), 1) * sizeof(gw::GroupTile)));
+  std::vector<gw::SplitDesc> wd(n_mol), yd(np);
+  for (int j = 0; j < n_tau; ++j) {
+    // W(tau_j) of every molecule: magnitudes, then slices
+    const double* w64 = nullptr;
+    if (w_on_device) {
+      // one contiguous view is needed: copy the molecules' matrices together
+      if (!b_w64.p) SB_TRY(cudaMalloc(&b_w64.p, std::max<long long>(nW, 1) * 8));
+      for (int i = 0; i < n_mol; ++i)
+        SB_TRY(cudaMemcpyAsync((double*)b_w64.p + offW[i], W_tau[i] + (size_t)j * ctxs[i]->nri * ctxs[i]->nri,
+                               (size_t)ctxs[i]->nri * ctxs[i]->nri * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+      for (int i = 0; i < n_mol; ++i)
+        SB_TRY(cudaMemcpyAsync((double*)b_w64.p + offW[i], W_tau[i] + (size_t)j * ctxs[i]->nri * ctxs[i]->nri,
+                               (size_t)ctxs[i]->nri * ctxs[i]->nri * 8, cudaMemcpyHostToDevice, st));
+    }
+    w64 = (const double*)b_w64.p;
+    for (int i = 0; i < n_mol; ++i)
+      wd[i] = gw::SplitDesc{offW[i], offWrow[i], ctxs[i]->nri, ctxs[i]->nri, ctxs[i]->nri, 0, 1.0};
+    std::vector<double> wmx(2 * n_mol, 1.0);
+    if (f16) {
+      SB_TRY(cudaMemcpyAsync(b_sd.p, wd.data(), n_mol * sizeof(gw::SplitDesc), cudaMemcpyHostToDevice, st));
+      gw::launch_absmax_group(w64, (const gw::SplitDesc*)b_sd.p, n_mol, max_nri, (double*)b_mx.p, st);
+      SB_TRY(cudaGetLastError());
+      SB_TRY(cudaMemcpyAsync(wmx.data(), b_mx.p, 2 * n_mol * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SB_TRY(cudaStreamSynchronize(st));
+    }
+    std::vector<double> s_w(n_mol, 1.0);
+    for (int i = 0; i < n_mol; ++i) {
+      if (f16) s_w[i] = gw::pow2_scale(wmx[2 * i]);
+      wd[i].scale = s_w[i];
+    }
+    SB_TRY(cudaMemcpyAsync(b_sd.p, wd.data(), n_mol * sizeof(gw::SplitDesc), cudaMemcpyHostToDevice, st));
+    gw::launch_split_group(w64, (const gw::SplitDesc*)b_sd.p, n_mol, max_nri, kmax, slices, ws_elems, f16,
+                           b_ws.p, st);
+    SB_TRY(cudaGetLastError());
+    // product 1, every problem in one launch: Y_p = -(B_p W)
+    size_t k = 0;
+    for (int p = 0; p < np; ++p) {
+      const Prob& q = pr[p];
+      const float sc = (float)(1.0 / (s_b[p] * s_w[q.mol]));
+      for (int mt = 0; mt * tile < q.nao; ++mt)
+        for (int nt = 0; nt * tile < q.nri; ++nt) t1[k++].scale = sc;
+    }
+    SB_TRY(cudaMemcpyAsync(b_t1.p, t1.data(), t1.size() * sizeof(gw::GroupTile), cudaMemcpyHostToDevice, st));
+    SB_TRY(cudaMemsetAsync(b_y64.p, 0, std::max<long long>(nY, 1) * 8, st));
+    if (gw::launch_group_tc(slices, f16, m_b, m_w, (const gw::GroupTile*)b_t1.p, (int)t1.size(),
+                            (double*)b_y64.p, c0->flush_k, (int*)b_err.p, st)) {
+      c0->err = "gw_sigma_tau_batch: tensor-core launch setup failed";
+      return GW_ERR_CUDA;
+    }
+    SB_TRY(cudaGetLastError());
+    // Y slices with the bound |B W| <= max_mu sum_P |B[mu][P]| * max |W|
+    std::vector<double> s_y(np, 1.0);
+    for (int p = 0; p < np; ++p) {
+      if (f16) s_y[p] = gw::pow2_scale(bmx[2 * p + 1] * wmx[2 * pr[p].mol]);
+      yd[p] = gw::SplitDesc{pr[p].offY, pr[p].rowB, pr[p].nao, pr[p].nri, pr[p].nri, 0, s_y[p]};
+    }
+    SB_TRY(cudaMemcpyAsync(b_sd.p, yd.data(), np * sizeof(gw::SplitDesc), cudaMemcpyHostToDevice, st));
+    gw::launch_split_group((const double*)b_y64.p, (const gw::SplitDesc*)b_sd.p, np, max_nao, kmax, slices,
+                           bs_elems, f16, b_ys.p, st);
+    SB_TRY(cudaGetLastError());
+    // product 2: Z_p = -(Y_p B_p^T) = B_p W B_p^T
+    k = 0;
+    for (int p = 0; p < np; ++p) {
+      const Prob& q = pr[p];
+      const float sc = (float)(1.0 / (s_y[p] * s_b[p]));
+      for (int mt = 0; mt * tile < q.nao; ++mt)
+        for (int nt = 0; nt * tile < q.nao; ++nt) t2[k++].scale = sc;
+    }
+    SB_TRY(cudaMemcpyAsync(b_t2.p, t2.data(), t2.size() * sizeof(gw::GroupTile), cudaMemcpyHostToDevice, st));
+    SB_TRY(cudaMemsetAsync(b_z64.p, 0, std::max<long long>(nZ, 1) * 8, st));
+    if (gw::launch_group_tc(slices, f16, m_y, m_b, (const gw::GroupTile*)b_t2.p, (int)t2.size(),
+                            (double*)b_z64.p, c0->flush_k, (int*)b_err.p, st)) {
+      c0->err = "gw_sigma_tau_batch: tensor-core launch setup failed";
+      return GW_ERR_CUDA;
+    }
+    SB_TRY(cudaGetLastError());
+    // Green's functions of every molecule at its tau_j (FP64, filtered)
+    for (int i = 0; i < n_mol; ++i) {
+      const gw_ctx* c = ctxs[i];
+      gw::launch_greens(c->d_C, c->d_eps, c->nao, c->n_occ, c->mu, c->tau[j], (double*)b_cso.p,
+                        (double*)b_csv.p, (double*)b_go.p + offG[i], (double*)b_gv.p + offG[i], st);
+      if (thr > 0.0) {
+        gw::launch_sym_block_filter((double*)b_go.p + offG[i], c->nao, c->d_ao_off, c->n_at, thr,
+                                    (unsigned char*)b_fl.p, st);
+        gw::launch_sym_block_filter((double*)b_gv.p + offG[i], c->nao, c->d_ao_off, c->n_at, thr,
+                                    (unsigned char*)b_fl.p, st);
+      }
+    }
+    SB_TRY(cudaGetLastError());
+    gw::sigma::k_dot2_group<<<dim3(kDotBlocks, np), 256, 0, st>>>((const double*)b_go.p, (const double*)b_gv.p,
+                                                                  (const double*)b_z64.p,
+                                                                  (const gw::sigma::DotDesc*)b_dd.p,
+                                                                  (double*)b_part.p);
+    SB_TRY(cudaGetLastError());
+    SB_TRY(cudaMemcpyAsync(part.data(), b_part.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
+    SB_TRY(cudaStreamSynchronize(st));
+    for (int p = 0; p < np; ++p) {
+      double so = 0.0, sv = 0.0;
+      for (int bl = 0; bl < kDotBlocks; ++bl) {
+        so += part[((size_t)p * kDotBlocks + bl) * 2];
+        sv += part[((size_t)p * kDotBlocks + bl) * 2 + 1];
+      }
+      double* o = sigma_out[pr[p].mol] + ((size_t)pr[p].a * n_tau + j) * 2;
+      o[0] = -so;
+      o[1] = sv;
+    }
+  }
+  int h_err = 0;
+  SB_TRY(cudaMemcpy(&h_err, b_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_err) {
+    c0->err = "gw_sigma_tau_batch: a bounded wait of the tensor-core kernel gave up";
+    return GW_ERR_TIMEOUT;
+  }
+  return GW_OK;
+}
+#undef SB_TRY
+
+}  // namespace
+
+extern "C" int gw_sigma_tau_batch(gw_ctx* const* ctxs, int n_mol, const double* const* W_tau, int w_on_device,
+                                  const int* const* orbitals, const int* n_orb, double thr, int precision,
+                                  double* const* sigma_out) {
+  if (!ctxs || n_mol <= 0 || !ctxs[0]) return GW_ERR_INVALID_ARG;
+  gw_ctx* c0 = ctxs[0];
+  gw::TraceRange trace("gw_sigma_tau_batch");
+  c0->err.clear();
+  if (!W_tau || !orbitals || !n_orb || !sigma_out || !(thr >= 0.0) || !std::isfinite(thr)) {
+    c0->err = "gw_sigma_tau_batch: bad arguments";
+    return GW_ERR_INVALID_ARG;
+  }
+  if (precision != GW_FP64 && precision != GW_BF16X3 && precision != GW_BF16X6 && precision != GW_FP16X3) {
+    c0->err = "gw_sigma_tau_batch: precision must be GW_FP64, GW_BF16X3, GW_BF16X6 or GW_FP16X3";
+    return GW_ERR_UNSUPPORTED;
+  }
+  for (int i = 0; i < n_mol; ++i) {
+    const gw_ctx* c = ctxs[i];
+    if (!c || !W_tau[i] || !orbitals[i] || !sigma_out[i] || n_orb[i] <= 0 || n_orb[i] > 1024) {
+      c0->err = "gw_sigma_tau_batch: bad arguments for molecule " + std::to_string(i);
+      return GW_ERR_INVALID_ARG;
+    }
+    if (c->n_at == 0 || c->blk_off.empty() || !c->have_greens) {
+      c0->err = "gw_sigma_tau_batch: molecule " + std::to_string(i) +
+                ": call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
+      return GW_ERR_ORDER;
+    }
+    if (c->device != c0->device || c->tau.size() != c0->tau.size()) {
+      c0->err = "gw_sigma_tau_batch: every context must be on the same device and have as many tau points";
+      return GW_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < n_orb[i]; ++a)
+      if (orbitals[i][a] < 0 || orbitals[i][a] >= c->nao) {
+        c0->err = "gw_sigma_tau_batch: orbital index out of range (molecule " + std::to_string(i) + ")";
+        return GW_ERR_INVALID_ARG;
+      }
+  }
+  if (cudaSetDevice(c0->device) != cudaSuccess) return GW_ERR_CUDA;
+  if (precision == GW_FP64) {
+    // the plain FP64 form, one molecule at a time
+    for (int i = 0; i < n_mol; ++i) {
+      gw_ctx* c = ctxs[i];
+      c->err.clear();
+      const int rc = sigma_impl(c, W_tau[i], w_on_device, orbitals[i], n_orb[i], thr, precision,
+                                c->tau.data(), (int)c->tau.size(), sigma_out[i]);
+      if (rc) {
+        c0->err = "gw_sigma_tau_batch: molecule " + std::to_string(i) + ": " + c->err;
+        return rc;
+      }
+    }
+    return GW_OK;
+  }
+  return sigma_batch_mixed(ctxs, n_mol, W_tau, w_on_device, orbitals, n_orb, thr, precision, sigma_out);
+}

@@ -382,6 +382,69 @@ struct ChiJob {
 };
 
 // ---------------------------------------------------------------------------
+// grouped products (the batched self-energy): independent problems of their
+// own sizes in one launch
+// ---------------------------------------------------------------------------
+struct GroupJob {
+  const GroupTile* tiles;
+  int n_tiles;
+  double* out;
+  static constexpr bool kPeriodic = true;
+  static constexpr bool kTileStaging = false;
+  static constexpr int kDrainHalves = 2;
+
+  struct Tile {
+    int ya, yb, idx;
+    long long ks;
+  };
+  __device__ Tile tile(int t) const {
+    const GroupTile& g = tiles[t];
+    Tile T;
+    T.ya = g.a_row;
+    T.yb = g.b_row;
+    T.idx = t;
+    T.ks = g.ksteps;
+    return T;
+  }
+  __device__ long long nsteps(const Tile& T) const { return T.ks; }
+  __device__ int items() const { return n_tiles; }
+  struct Iter {
+    int x;
+    __device__ void init(const GroupJob*, const Tile&) { x = 0; }
+    __device__ int next() {
+      const int v = x;
+      x += kStageK;
+      return v;
+    }
+  };
+  // out -= scale * acc through the warp's staging buffer (4 rows of 8
+  // consecutive doubles per store); one owner per tile
+  __device__ void write(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
+                        uint8_t* stg) const {
+    const GroupTile g = tiles[T.idx];
+    float* f = reinterpret_cast<float*>(stg);
+    constexpr int kRowsPer = 32 / kStgCols;
+#pragma unroll
+    for (int cc = 0; cc < kEpiCols; cc += kStgCols) {
+#pragma unroll
+      for (int j = 0; j < kStgCols; ++j) f[lane * kStgPitch + j] = acc[cc + j];
+      __syncwarp();
+      const int col = lane % kStgCols, sub = lane / kStgCols;
+      const int c = c0 + cc + col;
+#pragma unroll
+      for (int i = 0; i < 32 / kRowsPer; ++i) {
+        const int r = quad * 32 + kRowsPer * i + sub;
+        if (r < g.rows && c < g.cols) {
+          double* o = out + g.out_off + static_cast<long long>(r) * g.ld + c;
+          *o -= static_cast<double>(f[(kRowsPer * i + sub) * kStgPitch + col] * g.scale);
+        }
+      }
+      __syncwarp();
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
 // steps A / B job
 // ---------------------------------------------------------------------------
 // Adds each lane's ss into norm2[key] (key < 0: nothing).  Lanes with equal
@@ -1195,6 +1258,49 @@ __global__ void k_split_f64(const double* __restrict__ a, long long ld, int rows
   }
 }
 
+// Grouped split: problem p's FP64 matrix src[off + r * ld + k] (r < rows,
+// k < cols), times its scale, into slice rows dst_row + r of [S][..][kmax],
+// zero for k >= cols.  blockIdx.y = problem.
+__global__ void k_split_group(const double* __restrict__ src, const SplitDesc* __restrict__ desc,
+                              int kmax, int slices, long long slice_elems, int f16,
+                              uint16_t* __restrict__ out) {
+  const SplitDesc d = desc[blockIdx.y];
+  const long long n = static_cast<long long>(d.rows) * kmax;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i / kmax), k = static_cast<int>(i % kmax);
+    double v = k < d.cols ? d.scale * src[d.src_off + static_cast<long long>(r) * d.ld + k] : 0.0;
+    const long long dst = (d.dst_row + r) * kmax + k;
+    for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
+  }
+}
+
+// Grouped magnitudes: out[2p] = max |x|, out[2p + 1] = max over rows of
+// sum |x[r][:]| of problem p (out zeroed by the caller; non-negative doubles
+// order like their bit patterns).  A warp per row, blockIdx.y = problem.
+__global__ void k_absmax_group(const double* __restrict__ src, const SplitDesc* __restrict__ desc,
+                               unsigned long long* __restrict__ out) {
+  const SplitDesc d = desc[blockIdx.y];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  double mx = 0.0, rs_max = 0.0;
+  for (long long r = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + warp; r < d.rows;
+       r += static_cast<long long>(gridDim.x) * (blockDim.x / 32)) {
+    double rs = 0.0;
+    for (int c = lane; c < d.cols; c += 32) {
+      const double v = fabs(src[d.src_off + r * d.ld + c]);
+      rs += v;
+      mx = fmax(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    rs_max = fmax(rs_max, rs);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    atomicMax(out + 2 * blockIdx.y, static_cast<unsigned long long>(__double_as_longlong(mx)));
+    atomicMax(out + 2 * blockIdx.y + 1, static_cast<unsigned long long>(__double_as_longlong(rs_max)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // step-C work units planned on the device
 // ---------------------------------------------------------------------------
@@ -1509,6 +1615,39 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
   // mode 0: the panel rows are the A operand
   if (mode == 0) return launch_persistent(slices, f16, mp, mg, job, flush_k, err_flag, st);
   return launch_persistent(slices, f16, mg, mp, job, flush_k, err_flag, st);
+}
+
+void launch_split_group(const double* src, const SplitDesc* desc, int n_prob, int max_rows, int kmax,
+                        int slices, long long slice_elems, int f16, void* out, cudaStream_t st) {
+  if (n_prob == 0 || max_rows == 0) return;
+  long long bx = (static_cast<long long>(max_rows) * kmax + 255) / 256;
+  if (bx > 256) bx = 256;
+  for (int p0 = 0; p0 < n_prob; p0 += 65535) {
+    const int np = n_prob - p0 < 65535 ? n_prob - p0 : 65535;
+    tc::k_split_group<<<dim3(static_cast<unsigned>(bx), np), 256, 0, st>>>(
+        src, desc + p0, kmax, slices, slice_elems, f16, static_cast<uint16_t*>(out));
+  }
+}
+
+void launch_absmax_group(const double* src, const SplitDesc* desc, int n_prob, int max_rows, double* out2,
+                         cudaStream_t st) {
+  if (n_prob == 0) return;
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double) * n_prob, st);
+  int bx = (max_rows + 7) / 8;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  for (int p0 = 0; p0 < n_prob; p0 += 65535) {
+    const int np = n_prob - p0 < 65535 ? n_prob - p0 : 65535;
+    tc::k_absmax_group<<<dim3(bx, np), 256, 0, st>>>(src, desc + p0,
+                                                     reinterpret_cast<unsigned long long*>(out2) + 2 * p0);
+  }
+}
+
+int launch_group_tc(int slices, int f16, const CUtensorMap& ma, const CUtensorMap& mb,
+                    const GroupTile* tiles, int n_tiles, double* out, int flush_k, int* err_flag,
+                    cudaStream_t st) {
+  tc::GroupJob job{tiles, n_tiles, out};
+  return launch_persistent(slices, f16, ma, mb, job, flush_k, err_flag, st);
 }
 
 int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtensorMap& mg,

@@ -83,6 +83,36 @@ int launch_panel_tc(int slices, int f16, float unscale, float out_scale, const C
                     const int* atom_of_ri, const int* atom_of_ao, const int* ao_off, int n_at, int npa,
                     int pa0, int mu_base, int m_base, int nmc, int flush_k, int* err_flag,
                     cudaStream_t st);
+// One tile of a grouped product (GroupJob in k_tc.cu): out[off + r * ld + c]
+// -= scale * sum_{k < 64 ksteps} A[a_row + r][k] B[b_row + c][k] for
+// r < rows, c < cols (one owner per tile, FP64 read-modify-write).
+struct GroupTile {
+  long long out_off;
+  int a_row, b_row, ksteps, rows, cols, ld;
+  float scale;
+  int pad;
+};
+// One matrix of a grouped split / magnitude pass: FP64 rows [rows][cols]
+// (row stride ld) at src + src_off, written to slice rows dst_row.. with
+// factor scale.
+struct SplitDesc {
+  long long src_off, dst_row;
+  int rows, cols, ld, pad;
+  double scale;
+};
+// scale * matrix -> 16-bit slices [S][..][kmax] for every problem in one launch
+// (zero for k >= cols); max_rows bounds the problems' row counts.
+void launch_split_group(const double* src, const SplitDesc* desc, int n_prob, int max_rows, int kmax,
+                        int slices, long long slice_elems, int f16, void* out, cudaStream_t st);
+// out2[2p] = max |x|, out2[2p + 1] = max row sum |x| of every problem.
+void launch_absmax_group(const double* src, const SplitDesc* desc, int n_prob, int max_rows, double* out2,
+                         cudaStream_t st);
+// Many independent products of 16-bit slices in one persistent launch: A and
+// B are slices [S][rows][k_len] behind 3-D TMA maps, each tile reads its own
+// rows and reduction length and writes its own FP64 output block.
+int launch_group_tc(int slices, int f16, const CUtensorMap& ma, const CUtensorMap& mb,
+                    const GroupTile* tiles, int n_tiles, double* out, int flush_k, int* err_flag,
+                    cudaStream_t st);
 // Steps A/B with the staged epilogue (two slices; PanelStagedJob in k_tc.cu).
 // Tile entries (task, A row offset, B row offset, rows_valid << 16 |
 // cols_valid): mode 0 A = owner panel rows from a pw boundary, B = G^occ rows

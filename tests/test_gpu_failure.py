@@ -83,6 +83,9 @@ def test_allocation_failure_during_panel_rebuild_leaves_no_stale_cache(pkg):
         assert e.value.code == -5  # GW_ERR_OOM
         got = ctx.chi_tau(thr1, "fp64").cpu().numpy()
         assert _rel(got, ref) <= 1e-10
+        # (tau index 0: at tau = 50 a.u. every block is below thr1 and chi is zero)
         out = torch.full((ctx.nri, ctx.nri), float("nan"), dtype=torch.float64, device="cuda:0")
+        _lib.gw_chi_tau_noalloc(ctx.ctx, 0, thr1, out.data_ptr())
+        assert _rel([out.cpu().numpy()], [ref[0]]) <= 1e-10
         _lib.gw_chi_tau_noalloc(ctx.ctx, 1, thr1, out.data_ptr())
-        assert _rel([out.cpu().numpy()], [ref[1]]) <= 1e-10
+        assert not np.any(out.cpu().numpy()) and not np.any(ref[1])

@@ -60,7 +60,9 @@ def test_evgw_matches_oracle_and_restores_levels(pkg):
     print(f"evGW HOMO/LUMO {got} after {cycles} cycles; oracle {ref} after {ref_cycles}; "
           f"max |difference| {np.max(np.abs(got - ref)):.3e} Ha")
     assert abs(cycles - ref_cycles) <= 1
-    assert np.max(np.abs(got - ref)) < 1e-6
+    # the GB300 run differed from the oracle by 1.1e-11 Ha (the Pade continuation
+    # amplifies rounding-order differences); 1e-9 Ha leaves two decades of room
+    assert np.max(np.abs(got - ref)) < 1e-9
     # the context is back on the levels given to gw_set_greens
     chi_ref = oc.chi_dense(case, tau_index=0)[0]
     assert np.linalg.norm(chi[0] - chi_ref) <= 1e-10 * np.linalg.norm(chi_ref)

@@ -604,6 +604,77 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_sigma_batch(args):
+    """The batched self-energy workload: Sigma^c(+-i tau) of HOMO and LUMO for
+    64 molecules of 10-150 atoms (rings and ribbon segments, 20 tau points,
+    thr 1e-9, synthetic NSD W) through gw_sigma_tau_batch, the split form
+    against the plain FP64 form, with per-molecule errors against the block
+    oracle on a sample of molecules."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from oracle import sigma as osg
+    from paper_2104_09857_gb300 import Context, _lib
+    from synth import case_from_system, molecule_set
+    from synth.chain_inputs import synthetic_w
+
+    mols = molecule_set(64, 10, 150, 20210425)
+    ctxs, ws, orbs, sizes = [], [], [], []
+    t0 = time.perf_counter()
+    for i, m in enumerate(mols):
+        c = case_from_system(m, 20, 1e-9, 20210425 + i)
+        ctx = Context(0)
+        ctx.load_case(c)
+        ctxs.append(ctx)
+        ws.append(synthetic_w(c.system.nri_total, c.tau, 100 + i))
+        orbs.append([c.n_occ - 1, c.n_occ])
+        sizes.append((c.system.n_atoms, c.system.nao_total, c.system.nri_total))
+        del c
+    t_gen = time.perf_counter() - t0
+    handles = [c.ctx for c in ctxs]
+    # dense product flops of Eq. 10 per tau point: Y = B W and Z = Y B^T per orbital
+    flops_tau = sum(2 * len(o) * (ao * ri * ri + ao * ao * ri) for o, (_, ao, ri) in zip(orbs, sizes))
+    res = {}
+    outs = {}
+    for prec in (args.precision, "fp64"):
+        _lib.gw_sigma_tau_batch(handles, ws, orbs, 1e-9, _lib.PRECISIONS[prec])  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = _lib.gw_sigma_tau_batch(handles, ws, orbs, 1e-9, _lib.PRECISIONS[prec])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        outs[prec] = out
+        res[prec] = {"s_per_call": dt, "ms_per_tau": dt * 1e3 / 20, "tflops_dense_products": 20 * flops_tau / dt / 1e12}
+    for c in ctxs:
+        c.close()
+    # per-molecule error on a sample spread over the sizes (oracle on the host)
+    order = np.argsort([s_[0] for s_ in sizes])
+    pick = sorted({int(order[int(round(x))]) for x in np.linspace(0, 63, args.sigma_check)})
+    taus = [0, 9, 19]
+    errs = []
+    for i in pick:
+        c = case_from_system(mols[i], 20, 1e-9, 20210425 + i)
+        ref = osg.sigma_blocks(c, ws[i], orbs[i], taus)
+        sc = np.abs(ref).max()
+        errs.append({"molecule": i, "atoms": sizes[i][0],
+                     "err_" + args.precision: float(np.abs(outs[args.precision][i][:, taus] - ref).max() / sc),
+                     "err_fp64": float(np.abs(outs["fp64"][i][:, taus] - ref).max() / sc)})
+    line = {"metric": "batched Sigma^c(i tau) of HOMO/LUMO, 64 molecules, time per tau point",
+            "value": res[args.precision]["ms_per_tau"], "unit": "ms per tau point (all 64 molecules)",
+            "higher_is_better": False, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "64 molecules, 10-150 atoms (rings and ribbon segments), "
+                                   f"{sum(s_[1] for s_ in sizes)} AO / {sum(s_[2] for s_ in sizes)} RI in all, "
+                                   "20 tau, thr 1e-9, HOMO and LUMO"},
+            "forms": res, "speedup_split_over_fp64": res["fp64"]["s_per_call"] / res[args.precision]["s_per_call"],
+            "dense_product_flops_per_tau": flops_tau, "errors_vs_oracle": errs,
+            "max_err_split": max(e["err_" + args.precision] for e in errs),
+            "max_err_fp64": max(e["err_fp64"] for e in errs), "setup_s": t_gen}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,7 +703,12 @@ def main():
                     help="search the tensor-core schedule (gw_autotune) before the warm-up")
     ap.add_argument("--batch-bytes", type=float, default=0,
                     help="device bytes for one batch's X and Y operands (0: the library default)")
+    ap.add_argument("--sigma-check", type=int, default=6,
+                    help="batched self-energy workload: molecules checked against the oracle")
     args = ap.parse_args()
+    if args.workload == "molecules64":
+        run_sigma_batch(args)
+        return
     if args.peaks:
         import __graft_entry__ as g
 

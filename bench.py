@@ -475,6 +475,8 @@ def run_ours(args):
                    "parallelism": f"tau-sharded replicas x{world}"},
         "roofline": roof,
         "roofline_other": roof_other,
+        "step_flops": {"a": agg["flops_a"] / max(1, args.steps), "b": agg["flops_b"] / max(1, args.steps),
+                       "c": agg["flops_c"] / max(1, args.steps), "batches": agg["n_batches"] / max(1, args.steps)},
         "step_ms": {"greens": agg["ms_greens"] / max(1, args.steps),
                     "ab_kernels": agg["ms_step_ab"] / max(1, args.steps),
                     "c_kernel": agg["ms_step_c_kernel"] / max(1, args.steps)},

@@ -437,6 +437,14 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
  *                  (default 40e9)
  *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)
+ *   "tensor_fp32"  1: the next gw_set_3c_tensor keeps the device copy of the
+ *                  tensor in FP32 (half the bytes; block norms, finiteness
+ *                  and symmetry are still taken from the FP64 input).  Only
+ *                  the tensor-core forms can then run (the CUDA-core forms,
+ *                  the self-energies and the allocation-free entry point
+ *                  return GW_ERR_UNSUPPORTED or GW_ERR_ORDER); rounding T to
+ *                  FP32 (2^-24) is below the split forms' own representation
+ *                  error.  Default 0.
  *   "panel_staged" two-slice forms (FP16x3, BF16x3): 1 (default) steps A/B
  *                  stage each finished tile in shared memory and write whole
  *                  runs of X and Y; 0 per-element stores from registers

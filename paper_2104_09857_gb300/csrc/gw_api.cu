@@ -122,6 +122,8 @@ void free_dev(void* p) {
 
 void reset_tensor(gw_ctx* ctx) {
   free_dev(ctx->d_t3);
+  free_dev(ctx->d_t3f);
+  ctx->d_t3f = nullptr;
   free_dev(ctx->d_blk);
   free_dev(ctx->d_blk_off);
   free_dev(ctx->d_blk_norm);
@@ -268,6 +270,9 @@ int plan_panels(gw_ctx* ctx, double thr) {
 // The FP64 owner panels of the plan (the CUDA-core routes, the self-energy
 // and the allocation-free entry point).
 int build_panels(gw_ctx* ctx, double thr) {
+  if (ctx->d_t3f)
+    return fail(ctx, GW_ERR_UNSUPPORTED,
+                "the FP64 panels need the tensor in FP64 (it is kept in FP32: option tensor_fp32)");
   int rc;
   if ((rc = plan_panels(ctx, thr))) return rc;
   if (ctx->panels_ok && ctx->panels_thr == thr) return GW_OK;
@@ -847,18 +852,28 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
     double *st2, h[4] = {0, 0, 0, 0};
     if ((rc = wsT(ctx, "pt_absmax", 4, &st2))) return rc;
     const long long n = ctx->n_elems, nrow = n / 1024;
-    gw::launch_absmax_rowsum(ctx->d_t3, 1024, (int)nrow, 1024, st2, ctx->stream);
-    gw::launch_absmax_rowsum(ctx->d_t3 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
-                             (int)(n - nrow * 1024), st2 + 2, ctx->stream);
+    if (ctx->d_t3f) {
+      gw::launch_absmax_f32(ctx->d_t3f, n, st2, ctx->stream);
+      GW_TRY(cudaMemsetAsync(st2 + 2, 0, 2 * sizeof(double), ctx->stream));
+    } else {
+      gw::launch_absmax_rowsum(ctx->d_t3, 1024, (int)nrow, 1024, st2, ctx->stream);
+      gw::launch_absmax_rowsum(ctx->d_t3 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
+                               (int)(n - nrow * 1024), st2 + 2, ctx->stream);
+    }
     GW_CHECK_LAUNCH();
     GW_TRY(cudaMemcpyAsync(h, st2, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     GW_TRY(cudaStreamSynchronize(ctx->stream));
     ctx->t_absmax = std::max(h[0], h[2]);
     pt_scale = gw::pow2_scale(ctx->t_absmax);
   }
-  gw::launch_pt_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_kept, (long long)kept.size(),
-                        d_rowB, d_kB, d_rowA, d_kA, kmax, slices, rows * kmax, f16, pt_scale, ctx->d_pt,
-                        ctx->stream);
+  if (ctx->d_t3f)
+    gw::launch_pt_scatter_f32(ctx->d_t3f, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_kept,
+                              (long long)kept.size(), d_rowB, d_kB, d_rowA, d_kA, kmax, slices, rows * kmax,
+                              f16, pt_scale, ctx->d_pt, ctx->stream);
+  else
+    gw::launch_pt_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_kept, (long long)kept.size(),
+                          d_rowB, d_kB, d_rowA, d_kA, kmax, slices, rows * kmax, f16, pt_scale, ctx->d_pt,
+                          ctx->stream);
   GW_CHECK_LAUNCH();
   GW_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->pt_rows = rows;
@@ -1600,16 +1615,9 @@ int gw_set_3c_tensor(gw_ctx* ctx, long long n_blocks, const int* blk_abp, const 
   ctx->blk_off = off;
   ctx->n_blocks = n_blocks;
   ctx->n_elems = n_elems;
-  GW_TRY(cudaMalloc(&ctx->d_t3, std::max<long long>(n_elems, 1) * sizeof(double)));
   GW_TRY(cudaMalloc(&ctx->d_blk, std::max<long long>(3 * n_blocks, 1) * sizeof(int)));
   GW_TRY(cudaMalloc(&ctx->d_blk_off, (n_blocks + 1) * sizeof(long long)));
   GW_TRY(cudaMalloc(&ctx->d_blk_norm, std::max<long long>(n_blocks, 1) * sizeof(double)));
-  // copy in chunks of 1 GiB (pageable host memory)
-  const long long chunk = 1LL << 27;
-  for (long long i = 0; i < n_elems; i += chunk) {
-    long long n = std::min(chunk, n_elems - i);
-    GW_TRY(cudaMemcpyAsync(ctx->d_t3 + i, data + i, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  }
   if (n_blocks > 0) {
     GW_TRY(cudaMemcpyAsync(ctx->d_blk, blk_abp, 3 * n_blocks * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   }
@@ -1622,9 +1630,51 @@ int gw_set_3c_tensor(gw_ctx* ctx, long long n_blocks, const int* blk_abp, const 
   int *d_nao, *d_nri;
   if ((rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao))) return rc;
   if ((rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri))) return rc;
-  gw::launch_block_norms_3c(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, n_blocks,
-                            ctx->d_blk_norm, d_bad, ctx->stream);
-  GW_CHECK_LAUNCH();
+  if (!ctx->tensor_fp32) {
+    GW_TRY(cudaMalloc(&ctx->d_t3, std::max<long long>(n_elems, 1) * sizeof(double)));
+    // copy in chunks of 1 GiB (pageable host memory)
+    const long long chunk = 1LL << 27;
+    for (long long i = 0; i < n_elems; i += chunk) {
+      long long n = std::min(chunk, n_elems - i);
+      GW_TRY(cudaMemcpyAsync(ctx->d_t3 + i, data + i, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    gw::launch_block_norms_3c(ctx->d_t3, 0, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, n_blocks,
+                              ctx->d_blk_norm, d_bad, ctx->stream);
+    GW_CHECK_LAUNCH();
+  } else {
+    // FP32 copy on the device: runs of whole blocks (up to 1 GiB of FP64, or
+    // one block) pass through an FP64 staging buffer, where their norms,
+    // finiteness and symmetry are taken before the cast
+    GW_TRY(cudaMalloc(&ctx->d_t3f, std::max<long long>(n_elems, 1) * sizeof(float)));
+    const long long chunk = 1LL << 27;
+    long long max_run = 1;
+    for (long long b0 = 0; b0 < n_blocks;) {
+      long long b1 = b0 + 1;
+      while (b1 < n_blocks && off[b1 + 1] - off[b0] <= chunk) ++b1;
+      max_run = std::max(max_run, off[b1] - off[b0]);
+      b0 = b1;
+    }
+    double* stage;
+    if ((rc = wsT(ctx, "t3_stage", (size_t)max_run, &stage))) return rc;
+    for (long long b0 = 0; b0 < n_blocks;) {
+      long long b1 = b0 + 1;
+      while (b1 < n_blocks && off[b1 + 1] - off[b0] <= chunk) ++b1;
+      const long long n = off[b1] - off[b0];
+      GW_TRY(cudaMemcpyAsync(stage, data + off[b0], n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      gw::launch_block_norms_3c(stage, off[b0], ctx->d_blk + 3 * b0, ctx->d_blk_off + b0, d_nao, d_nri,
+                                b1 - b0, ctx->d_blk_norm + b0, d_bad, ctx->stream);
+      gw::launch_cast_f64_f32(stage, ctx->d_t3f + off[b0], n, ctx->stream);
+      GW_CHECK_LAUNCH();
+      b0 = b1;
+    }
+    // the staging buffer is needed only here
+    GW_TRY(cudaStreamSynchronize(ctx->stream));
+    auto it = ctx->work.find("t3_stage");
+    if (it != ctx->work.end()) {
+      cudaFree(it->second.first);
+      ctx->work.erase(it);
+    }
+  }
   int bad = 0;
   ctx->blk_norm.resize(n_blocks);
   GW_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1710,6 +1760,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
     ctx->flush_k = (int)value;
     return GW_OK;
   }
+  if (!strcmp(key, "tensor_fp32")) {
+    if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "tensor_fp32 must be 0 or 1");
+    ctx->tensor_fp32 = (int)value;
+    return GW_OK;
+  }
   if (!strcmp(key, "panel_staged")) {
     if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "panel_staged must be 0 or 1");
     ctx->panel_staged = (int)value;
@@ -1767,7 +1822,7 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
   if (!ctx) return GW_ERR_INVALID_ARG;
   gw::TraceRange trace("gw_chi_tau");
   ctx->err.clear();
-  if (ctx->n_at == 0 || ctx->d_t3 == nullptr && ctx->n_blocks > 0)
+  if (ctx->n_at == 0 || (ctx->d_t3 == nullptr && ctx->d_t3f == nullptr && ctx->n_blocks > 0))
     return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_basis and gw_set_3c_tensor first");
   if (ctx->blk_off.empty()) return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_3c_tensor first");
   if (!ctx->have_greens) return fail(ctx, GW_ERR_ORDER, "chi_tau: call gw_set_greens first");
@@ -1797,6 +1852,9 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     explicit StallScope(int on) { gw::tc_set_stall_test(on); }
     ~StallScope() { gw::tc_set_stall_test(0); }
   } stall_scope(ctx->test_stall);
+  if (!tc_prec && ctx->d_t3f)
+    return fail(ctx, GW_ERR_UNSUPPORTED,
+                "chi_tau: the tensor is kept in FP32 (option tensor_fp32); the CUDA-core forms need it in FP64");
   int rc;
   // the tensor-core route needs the panel plan only; the CUDA-core routes
   // also the FP64 panel pool

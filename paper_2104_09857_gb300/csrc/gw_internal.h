@@ -146,6 +146,8 @@ struct gw_ctx {
   std::vector<int> blk;              // 3 per block
   std::vector<long long> blk_off;    // n_blocks + 1
   double* d_t3 = nullptr;
+  float* d_t3f = nullptr;  // the tensor kept in FP32 instead (option tensor_fp32)
+  int tensor_fp32 = 0;     // option: applies at the next gw_set_3c_tensor
   int* d_blk = nullptr;
   long long* d_blk_off = nullptr;
   double* d_blk_norm = nullptr;

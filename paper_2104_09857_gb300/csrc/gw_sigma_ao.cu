@@ -85,6 +85,10 @@ extern "C" int gw_sigma_ao_tau(gw_ctx* ctx, const double* W_tau, int w_on_device
   if (!ctx) return GW_ERR_INVALID_ARG;
   gw::TraceRange trace("gw_sigma_ao_tau");
   ctx->err.clear();
+  if (ctx->d_t3f) {
+    ctx->err = "gw_sigma_ao_tau: the tensor is kept in FP32 (option tensor_fp32); this route needs it in FP64";
+    return GW_ERR_UNSUPPORTED;
+  }
   if (!ctx->have_greens || ctx->n_at == 0 || (ctx->n_blocks > 0 && ctx->d_t3 == nullptr)) {
     ctx->err = "gw_sigma_ao_tau: call gw_set_basis, gw_set_3c_tensor and gw_set_greens first";
     return GW_ERR_ORDER;

@@ -15,14 +15,14 @@ namespace gw {
 // three-centre tensor: per-block Frobenius norm, finiteness, symmetry of
 // (A, A, P) blocks
 // ---------------------------------------------------------------------------
-__global__ void k_block_norms_3c(const double* __restrict__ t3, const int* __restrict__ blk,
-                                 const long long* __restrict__ off, const int* __restrict__ n_ao,
-                                 const int* __restrict__ n_ri, long long n_blocks,
-                                 double* __restrict__ norms, int* __restrict__ bad) {
+__global__ void k_block_norms_3c(const double* __restrict__ t3, long long base_off,
+                                 const int* __restrict__ blk, const long long* __restrict__ off,
+                                 const int* __restrict__ n_ao, const int* __restrict__ n_ri,
+                                 long long n_blocks, double* __restrict__ norms, int* __restrict__ bad) {
   long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (b >= n_blocks) return;
-  const double* x = t3 + off[b];
+  const double* x = t3 + (off[b] - base_off);
   long long n = off[b + 1] - off[b];
   double s = 0.0;
   bool nonfinite = false;
@@ -482,12 +482,13 @@ __global__ void k_mirror(const double* __restrict__ acc, double* __restrict__ ou
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-void launch_block_norms_3c(const double* t3, const int* blk, const long long* off, const int* n_ao,
-                           const int* n_ri, long long n_blocks, double* norms, int* bad,
+void launch_block_norms_3c(const double* t3, long long base_off, const int* blk, const long long* off,
+                           const int* n_ao, const int* n_ri, long long n_blocks, double* norms, int* bad,
                            cudaStream_t st) {
   if (n_blocks == 0) return;
   long long grid = (n_blocks + 7) / 8;
-  k_block_norms_3c<<<(unsigned)grid, 256, 0, st>>>(t3, blk, off, n_ao, n_ri, n_blocks, norms, bad);
+  k_block_norms_3c<<<(unsigned)grid, 256, 0, st>>>(t3, base_off, blk, off, n_ao, n_ri, n_blocks, norms,
+                                                    bad);
 }
 
 void launch_panel_scatter(const double* t3, const int* blk, const long long* off, const int* n_ao,

@@ -7,8 +7,10 @@
 
 namespace gw {
 
-void launch_block_norms_3c(const double* t3, const int* blk, const long long* off, const int* n_ao,
-                           const int* n_ri, long long n_blocks, double* norms, int* bad,
+// Per-block Frobenius norms, finiteness and (A, A, P) symmetry of blocks
+// [0, n_blocks) of blk/off; block b's data starts at t3 + off[b] - base_off.
+void launch_block_norms_3c(const double* t3, long long base_off, const int* blk, const long long* off,
+                           const int* n_ao, const int* n_ri, long long n_blocks, double* norms, int* bad,
                            cudaStream_t st);
 void launch_panel_scatter(const double* t3, const int* blk, const long long* off, const int* n_ao,
                           const int* n_ri, const int* ri_off, const int* kept_idx, int n_kept,

@@ -1111,7 +1111,8 @@ __global__ void k_gather_g(const double* __restrict__ g, int nao, const PanelTas
 // (T symmetric in its primary indices).  Consecutive threads take
 // consecutive columns of a row.  One CTA per kept block, striding; the
 // buffer is zeroed beforehand (padding and blocks not stored).
-__global__ void k_pt_scatter(const double* __restrict__ t3, const int* __restrict__ blk,
+template <typename T>
+__global__ void k_pt_scatter(const T* __restrict__ t3, const int* __restrict__ blk,
                              const long long* __restrict__ off, const int* __restrict__ n_ao,
                              const int* __restrict__ n_ri, const int* __restrict__ kept,
                              long long n_kept, const long long* __restrict__ rowB,
@@ -1122,14 +1123,14 @@ __global__ void k_pt_scatter(const double* __restrict__ t3, const int* __restric
     const int b = kept[kb];
     const int A = blk[3 * b], B = blk[3 * b + 1], p = blk[3 * b + 2];
     const int na = n_ao[A], nb = n_ao[B], np = n_ri[p];
-    const double* x = t3 + off[b];
+    const T* x = t3 + off[b];
     const long long n = static_cast<long long>(na) * nb * np;
     // panel B: i = (P' nb + sigma') na + lambda'
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
       const int al = static_cast<int>(i % na);
       const long long r = i / na;  // P' nb + sigma'
       const int be = static_cast<int>(r % nb), pl = static_cast<int>(r / nb);
-      double v = scale * x[(static_cast<long long>(al) * nb + be) * np + pl];
+      double v = scale * static_cast<double>(x[(static_cast<long long>(al) * nb + be) * np + pl]);
       const long long dst = (rowB[kb] + r) * kmax + kB[kb] + al;
       for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
     }
@@ -1139,7 +1140,7 @@ __global__ void k_pt_scatter(const double* __restrict__ t3, const int* __restric
       const int be = static_cast<int>(i % nb);
       const long long r = i / nb;  // P' na + lambda'
       const int al = static_cast<int>(r % na), pl = static_cast<int>(r / na);
-      double v = scale * x[(static_cast<long long>(al) * nb + be) * np + pl];
+      double v = scale * static_cast<double>(x[(static_cast<long long>(al) * nb + be) * np + pl]);
       const long long dst = (rowA[kb] + r) * kmax + kA[kb] + be;
       for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
     }
@@ -1403,6 +1404,17 @@ __global__ void k_units_scatter(const int* __restrict__ n_units, const int* __re
     u_first[pos] = t_first[u];
     u_count[pos] = t_count[u];
   }
+}
+
+// out[0] = max |x| of an FP32 array (as a double; out zeroed by the caller).
+__global__ void k_absmax_f32(const float* __restrict__ x, long long n, unsigned long long* __restrict__ out) {
+  float mx = 0.f;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    mx = fmaxf(mx, fabsf(x[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(mx))));
 }
 
 // out[0] = max |a|, out[1] = max over rows of sum |a[r][:]| (out zeroed by
@@ -1684,10 +1696,29 @@ void launch_pt_scatter(const double* t3, const int* blk, const long long* off, c
                        long long slice_elems, int f16, double scale, void* out, cudaStream_t st) {
   if (n_kept == 0) return;
   const long long grid = n_kept < 152LL * 64 ? n_kept : 152LL * 64;
-  tc::k_pt_scatter<<<static_cast<unsigned>(grid), 128, 0, st>>>(t3, blk, off, n_ao, n_ri, kept, n_kept,
-                                                               rowB, kB, rowA, kA, kmax, slices,
-                                                               slice_elems, f16, scale,
-                                                               static_cast<uint16_t*>(out));
+  tc::k_pt_scatter<double><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+      t3, blk, off, n_ao, n_ri, kept, n_kept, rowB, kB, rowA, kA, kmax, slices, slice_elems, f16, scale,
+      static_cast<uint16_t*>(out));
+}
+
+void launch_pt_scatter_f32(const float* t3, const int* blk, const long long* off, const int* n_ao,
+                           const int* n_ri, const int* kept, long long n_kept, const long long* rowB,
+                           const int* kB, const long long* rowA, const int* kA, int kmax, int slices,
+                           long long slice_elems, int f16, double scale, void* out, cudaStream_t st) {
+  if (n_kept == 0) return;
+  const long long grid = n_kept < 152LL * 64 ? n_kept : 152LL * 64;
+  tc::k_pt_scatter<float><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+      t3, blk, off, n_ao, n_ri, kept, n_kept, rowB, kB, rowA, kA, kmax, slices, slice_elems, f16, scale,
+      static_cast<uint16_t*>(out));
+}
+
+void launch_absmax_f32(const float* x, long long n, double* out2, cudaStream_t st) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+  if (n <= 0) return;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  tc::k_absmax_f32<<<static_cast<unsigned>(blocks), 256, 0, st>>>(x, n,
+                                                                 reinterpret_cast<unsigned long long*>(out2));
 }
 
 void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long long ldk, int rowoff,

@@ -143,6 +143,13 @@ void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpa
 void launch_gather_g(const double* g, int nao, const PanelTaskTC* tasks, int ntasks, const int* lam,
                      int rbase, int rows_valid, int rows_per_task, int kmax, int slices,
                      long long slice_elems, int f16, double scale, void* out, cudaStream_t st);
+// The same from the tensor kept in FP32 (option tensor_fp32).
+void launch_pt_scatter_f32(const float* t3, const int* blk, const long long* off, const int* n_ao,
+                           const int* n_ri, const int* kept, long long n_kept, const long long* rowB,
+                           const int* kB, const long long* rowA, const int* kA, int kmax, int slices,
+                           long long slice_elems, int f16, double scale, void* out, cudaStream_t st);
+// out2[0] = max |x| of an FP32 array (out2[1] untouched but zeroed).
+void launch_absmax_f32(const float* x, long long n, double* out2, cudaStream_t st);
 // Split, transposed owner panels [slices][rows][kmax] straight from the
 // kept 3c blocks (see k_pt_scatter); out must be zeroed beforehand.
 void launch_pt_scatter(const double* t3, const int* blk, const long long* off, const int* n_ao,

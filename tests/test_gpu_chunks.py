@@ -129,3 +129,24 @@ def test_autotune_keeps_the_fastest_schedule_and_the_result(lib):
     assert best <= trials[0]["ms"]
     assert all(t["ms"] > 0 for t in trials)
     _check(got, ref, 1e-6)
+
+
+def test_tensor_kept_in_fp32(lib):
+    """With the tensor kept in FP32 on the device the split forms still match
+    the oracle within 1e-6 and count the same useful flops (the filter
+    decisions come from the FP64 input); the FP64 form is refused."""
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("ribbon28", n_tau=3)
+    ref = oc.chi_dense(case)
+    a, sa = _run(lib, case, "fp16x3", case.thr, {"tensor_fp32": 1, "mu_chunk_atoms": 7})
+    b, sb = _run(lib, case, "fp16x3", case.thr, {"mu_chunk_atoms": 7})
+    _check(a, ref, 1e-6)
+    for k in ("flops_a", "flops_b", "flops_c"):
+        assert sa[k] == sb[k]
+    with lib.Context(0) as ctx:
+        ctx.set_option("tensor_fp32", 1)
+        ctx.load_case(case)
+        with pytest.raises(_lib.GwError) as e:
+            ctx.chi_tau(case.thr, "fp64", 0, 1)
+        assert e.value.code == -9

@@ -445,7 +445,7 @@ std::vector<Batch> plan_batches_tc(gw_ctx* ctx, size_t elem_bytes, double budget
     const int nmu = ctx->ao_off[m1] - ctx->ao_off[m0];
     return (nmu + kSlabAO - 1) / kSlabAO * kSlabAO;
   };
-  int cs = ctx->mlp_mode ? n : ctx->mu_chunk_atoms;
+  int cs = ctx->mu_chunk_atoms;
   if (cs <= 0 || cs > n) {
     // fewest equal chunks for which one owner's operands stay within a
     // budget share of 1/8 (so that batches hold several owners)
@@ -1218,6 +1218,14 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     mb.pa0 = pa0;
     mb.npa = npa;
     mb.slices = slices;
+    mb.m0 = b.m0;
+    mb.nmc = nmc;
+    mb.mu0 = b.mu0;
+    mb.nmu = b.nmu;
+    mb.Q0 = b.Q0;
+    mb.qrow = qrow;
+    mb.qa0 = qa0;
+    mb.nqa = nqa;
     mb.f16 = f16;
     mb.xinv = (float)(1.0 / s_x);
     mb.yinv = (float)(1.0 / s_y);

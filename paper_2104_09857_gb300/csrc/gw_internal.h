@@ -106,6 +106,8 @@ int build_panels_for(gw_ctx* ctx, double thr);
 // the network predicts below thr (minus the margin) from the lists.
 struct MlpBatch {
   int s0, ns, P0, prow, nslab, npt, nqt, tile, per, pa0, npa, slices;
+  int m0, nmc, mu0, nmu;  // mu-atom chunk and its AOs
+  int Q0, qrow, qa0, nqa; // Y rows (RI functions) and their RI atoms
   int f16;           // slices in binary16 holding X / xinv and Y / yinv
   float xinv, yinv;
   long long Kb;

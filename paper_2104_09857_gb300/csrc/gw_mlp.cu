@@ -76,11 +76,11 @@ int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb) {
   DevBuf xn, yn, cp, cq, cc, xyz, feat, aux, skipped;
   ML_TRY(cudaMalloc(&xn.p, (size_t)mb.nslab * mb.npt * sizeof(float)));
   ML_TRY(cudaMalloc(&yn.p, (size_t)mb.nslab * mb.nqt * sizeof(float)));
-  gw::mlp_slab_tile_norms(mb.bx2, mb.bx, ctx->n_at, mb.npa, mb.pa0, mb.per, kSlabAO, ctx->d_atom_of_ao,
-                          ctx->d_atom_of_ri, ctx->nao, mb.P0, mb.prow, mb.npt, mb.tile, mb.nslab,
+  gw::mlp_slab_tile_norms(mb.bx2, mb.bx, mb.nmc, mb.m0, mb.npa, mb.pa0, mb.per, kSlabAO, ctx->d_atom_of_ao,
+                          ctx->d_atom_of_ri, mb.mu0, mb.nmu, mb.P0, mb.prow, mb.npt, mb.tile, mb.nslab,
                           (float*)xn.p, st);
-  gw::mlp_slab_tile_norms(mb.by2, mb.by, ctx->n_at, ctx->n_at, 0, mb.per, kSlabAO, ctx->d_atom_of_ao,
-                          ctx->d_atom_of_ri, ctx->nao, 0, ctx->nri, mb.nqt, mb.tile, mb.nslab,
+  gw::mlp_slab_tile_norms(mb.by2, mb.by, mb.nmc, mb.m0, mb.nqa, mb.qa0, mb.per, kSlabAO, ctx->d_atom_of_ao,
+                          ctx->d_atom_of_ri, mb.mu0, mb.nmu, mb.Q0, mb.qrow, mb.nqt, mb.tile, mb.nslab,
                           (float*)yn.p, st);
   // centroids of row tiles, column tiles and AO chunks (weighted by functions)
   auto centroid = [&](const std::vector<int>& off, int lo, int hi, float* out3) {
@@ -103,9 +103,11 @@ int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb) {
   for (int t = 0; t < mb.npt; ++t)
     centroid(ctx->ri_off, mb.P0 + t * mb.tile, std::min(mb.P0 + mb.prow, mb.P0 + (t + 1) * mb.tile), &h_cp[3 * t]);
   for (int t = 0; t < mb.nqt; ++t)
-    centroid(ctx->ri_off, t * mb.tile, std::min(ctx->nri, (t + 1) * mb.tile), &h_cq[3 * t]);
+    centroid(ctx->ri_off, mb.Q0 + t * mb.tile, std::min(mb.Q0 + mb.qrow, mb.Q0 + (t + 1) * mb.tile),
+             &h_cq[3 * t]);
   for (int c = 0; c < mb.per; ++c)
-    centroid(ctx->ao_off, c * kSlabAO, std::min(ctx->nao, (c + 1) * kSlabAO), &h_cc[3 * c]);
+    centroid(ctx->ao_off, mb.mu0 + c * kSlabAO, std::min(mb.mu0 + mb.nmu, mb.mu0 + (c + 1) * kSlabAO),
+             &h_cc[3 * c]);
   for (int i = 0; i < 3 * ctx->n_at; ++i) h_xyz[i] = (float)ctx->xyz[i];
   ML_TRY(cudaMalloc(&cp.p, h_cp.size() * 4));
   ML_TRY(cudaMalloc(&cq.p, h_cq.size() * 4));
@@ -135,8 +137,8 @@ int mlp_batch_hook(gw_ctx* ctx, const MlpBatch& mb) {
   }
   if (ctx->mlp_mode == 1) {
     gw::mlp_task_norms(mb.xs, mb.ys, mb.slices, mb.f16, mb.xinv, mb.yinv, (long long)mb.prow * mb.Kb,
-                       (long long)ctx->nri * mb.Kb,
-                       mb.Kb, mb.prow, ctx->nri, mb.tasks, mb.counts, mb.nslab, mb.npt, mb.nqt, max_count,
+                       (long long)mb.qrow * mb.Kb,
+                       mb.Kb, mb.prow, mb.qrow, mb.tasks, mb.counts, mb.nslab, mb.npt, mb.nqt, max_count,
                        mb.tile, mb.slab_k0, mb.slab_len, (float*)aux.p, st);
     ML_TRY(cudaGetLastError());
     std::vector<float> h_feat((size_t)slots * F), h_tgt(slots);

@@ -24,24 +24,27 @@ constexpr int oW1 = 0, oB1 = H * F, oW2 = oB1 + H, oB2 = oW2 + H * H, oW3 = oB2 
 // ---------------------------------------------------------------------------
 // norm of the X part of (slab, row tile) and of the Y part of (slab, col tile)
 // from the kept blocks' squared norms
+// (mu-atom chunk [mc0, mc0 + nmc) with AOs [mu0, mu0 + nmu); slab c covers
+// chunk-local AOs [c naop_chunk, (c + 1) naop_chunk); block flags and norms
+// are [sigma-atom][mu-atom of the chunk][RI atom from pa0])
 __global__ void k_slab_tile_norms(const float* __restrict__ norm2, const unsigned char* __restrict__ flag,
-                                  int n_at, int npa, int pa0, int per, int naop_chunk,
+                                  int nmc, int mc0, int npa, int pa0, int per, int naop_chunk,
                                   const int* __restrict__ atom_of_ao, const int* __restrict__ atom_of_ri,
-                                  int nao, int row0, int rows, int ntile, int tile, int nslab,
+                                  int mu0, int nmu, int row0, int rows, int ntile, int tile, int nslab,
                                   float* __restrict__ out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<long long>(nslab) * ntile) return;
   const int t = static_cast<int>(i % ntile), slab = static_cast<int>(i / ntile);
   const int sl = slab / per, c = slab % per;
-  const int a_lo = c * naop_chunk, a_hi = min(nao, (c + 1) * naop_chunk) - 1;
+  const int a_lo = c * naop_chunk, a_hi = min(nmu, (c + 1) * naop_chunk) - 1;
   float s = 0.f;
-  if (a_lo < nao) {
-    const int m0 = atom_of_ao[a_lo], m1 = atom_of_ao[a_hi];
+  if (a_lo < nmu) {
+    const int m0 = atom_of_ao[mu0 + a_lo], m1 = atom_of_ao[mu0 + a_hi];
     const int r_lo = row0 + t * tile, r_hi = min(row0 + rows, row0 + (t + 1) * tile) - 1;
     const int p0 = atom_of_ri[r_lo], p1 = atom_of_ri[r_hi];
     for (int m = m0; m <= m1; ++m)
       for (int p = p0; p <= p1; ++p) {
-        const long long b = (static_cast<long long>(sl) * n_at + m) * npa + (p - pa0);
+        const long long b = (static_cast<long long>(sl) * nmc + (m - mc0)) * npa + (p - pa0);
         if (flag[b]) s += norm2[b];
       }
   }
@@ -315,14 +318,15 @@ __global__ void k_compact(int* __restrict__ tasks, int* __restrict__ counts, lon
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void mlp_slab_tile_norms(const float* norm2, const unsigned char* flag, int n_at, int npa, int pa0,
-                         int per, int naop_chunk, const int* atom_of_ao, const int* atom_of_ri, int nao,
-                         int row0, int rows, int ntile, int tile, int nslab, float* out, cudaStream_t st) {
+void mlp_slab_tile_norms(const float* norm2, const unsigned char* flag, int nmc, int mc0, int npa, int pa0,
+                         int per, int naop_chunk, const int* atom_of_ao, const int* atom_of_ri, int mu0,
+                         int nmu, int row0, int rows, int ntile, int tile, int nslab, float* out,
+                         cudaStream_t st) {
   const long long n = static_cast<long long>(nslab) * ntile;
   if (n == 0) return;
   mlp::k_slab_tile_norms<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(
-      norm2, flag, n_at, npa, pa0, per, naop_chunk, atom_of_ao, atom_of_ri, nao, row0, rows, ntile,
-      tile, nslab, out);
+      norm2, flag, nmc, mc0, npa, pa0, per, naop_chunk, atom_of_ao, atom_of_ri, mu0, nmu, row0, rows,
+      ntile, tile, nslab, out);
 }
 
 void mlp_task_features(const int* tasks, const int* counts, int nslab, int npt, int nqt, int per, int s0,

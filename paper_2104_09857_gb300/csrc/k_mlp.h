@@ -11,9 +11,13 @@ constexpr int kMlpBound = 7;  // feature index of log10(norm-product bound)
 constexpr int kMlpParams = kMlpHidden * kMlpFeatures + kMlpHidden + kMlpHidden * kMlpHidden +
                            kMlpHidden + kMlpHidden + 1;
 
-void mlp_slab_tile_norms(const float* norm2, const unsigned char* flag, int n_at, int npa, int pa0,
-                         int per, int naop_chunk, const int* atom_of_ao, const int* atom_of_ri, int nao,
-                         int row0, int rows, int ntile, int tile, int nslab, float* out, cudaStream_t st);
+// Norm of the X (or Y) part of every (slab, row tile): flags and squared
+// norms [sigma-atom][mu-atom of the chunk [mc0, mc0 + nmc)][RI atom from
+// pa0]; the chunk's AOs are [mu0, mu0 + nmu); tiles of `tile` rows from row0.
+void mlp_slab_tile_norms(const float* norm2, const unsigned char* flag, int nmc, int mc0, int npa, int pa0,
+                         int per, int naop_chunk, const int* atom_of_ao, const int* atom_of_ri, int mu0,
+                         int nmu, int row0, int rows, int ntile, int tile, int nslab, float* out,
+                         cudaStream_t st);
 void mlp_task_features(const int* tasks, const int* counts, int nslab, int npt, int nqt, int per, int s0,
                        const float* xn, const float* yn, const float* cent_p, const float* cent_q,
                        const float* cent_c, const float* xyz, const int* n_ao, float log_tau,

@@ -150,3 +150,26 @@ def test_tensor_kept_in_fp32(lib):
         with pytest.raises(_lib.GwError) as e:
             ctx.chi_tau(case.thr, "fp64", 0, 1)
         assert e.value.code == -9
+
+
+def test_learned_screening_with_chunks(lib):
+    """The learned screen on 2-D batches (7-atom mu chunks): the logged task
+    features and targets feed the same network, and the screened chi stays
+    within 1e-6 of the oracle at thr 1e-9."""
+    from paper_2104_09857_gb300 import _lib
+
+    case = make_case("ribbon28", n_tau=3)
+    ref = oc.chi_dense(case)
+    with lib.Context(0) as ctx:
+        ctx.set_option("mu_chunk_atoms", 7)
+        ctx.load_case(case)
+        feat, tgt = _lib.gw_mlp_log(ctx.ctx, 0, 3, case.thr, _lib.GW_FP16X3)
+        keep = tgt > -39.0
+        assert feat.shape[0] > 100 and np.all(tgt[keep] <= feat[keep, 7] + 1e-3)
+        _lib.gw_mlp_init(ctx.ctx, 17)
+        _lib.gw_mlp_train(ctx.ctx, feat[keep], tgt[keep], epochs=200, batch=0, lr=3e-3, seed=5)
+        ctx.set_option("mlp_margin", float(np.max(tgt[keep] - _lib.gw_mlp_predict(ctx.ctx, feat[keep]))) + 0.25)
+        got = ctx.chi_tau(case.thr, "fp16x3", screening=lib.GW_SCREEN_MLP).cpu().numpy()
+        st = ctx.stats()
+    assert st["n_batches"] > 1 and st["tasks_seen"] > 0
+    _check(got, ref, 1e-6)

@@ -437,6 +437,11 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *   "batch_bytes"  device bytes allowed for the per-batch X and Y operands
  *                  (default 40e9)
  *   "batch_atoms"  upper limit on sigma-atoms per batch (0 = no limit)
+ *   "panel_stream" split forms: 1 builds the split panels per operand batch
+ *                  (the owners' for step A, the chunk's atoms' for step B)
+ *                  instead of keeping the whole set resident; 0 (default)
+ *                  streams only when the whole set, the batch budget, chi and
+ *                  the Green's functions do not fit in free device memory
  *   "tensor_fp32"  1: the next gw_set_3c_tensor keeps the device copy of the
  *                  tensor in FP32 (half the bytes; block norms, finiteness
  *                  and symmetry are still taken from the FP64 input).  Only

@@ -92,6 +92,7 @@ int ws(gw_ctx* ctx, const char* name, size_t bytes, void** out) {
 // buffer sizes, so that two routes' operands are never resident together)
 void ws_release_all(gw_ctx* ctx) {
   auto& wb = ctx->work;
+  ctx->ptB_m0 = ctx->ptB_m1 = -1;  // a streamed panel region lives in a work buffer
   if (wb.empty()) return;
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : wb) cudaFree(kv.second.first);
@@ -229,6 +230,24 @@ int plan_panels(gw_ctx* ctx, double thr) {
   }
   ctx->panel_elems = off;
   ctx->lam_total = (long long)lam.size();
+  // per atom: the kept blocks in which it is an owner (B, or A != B)
+  ctx->plan_atom_off.assign(n + 1, 0);
+  for (int b : kept) {
+    const int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1];
+    ++ctx->plan_atom_off[B + 1];
+    if (A != B) ++ctx->plan_atom_off[A + 1];
+  }
+  for (int a = 0; a < n; ++a) ctx->plan_atom_off[a + 1] += ctx->plan_atom_off[a];
+  {
+    std::vector<int> fill(ctx->plan_atom_off.begin(), ctx->plan_atom_off.end() - 1);
+    ctx->plan_atom_blk.assign(ctx->plan_atom_off[n], 0);
+    for (size_t i = 0; i < kept.size(); ++i) {
+      const int b = kept[i];
+      const int A = ctx->blk[3 * b], B = ctx->blk[3 * b + 1];
+      ctx->plan_atom_blk[fill[B]++] = (int)i;
+      if (A != B) ctx->plan_atom_blk[fill[A]++] = (int)i;
+    }
+  }
   // flop weights of steps A and B per (owner, lambda-atom)
   {
     std::vector<std::map<int, double>> wl(n);
@@ -822,6 +841,46 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
     ctx->pt_tasks[s] = t;
   }
   if (rows > INT32_MAX) return fail(ctx, GW_ERR_INVALID_ARG, "transposed panels exceed 2^31 rows");
+  ctx->ptB_m0 = ctx->ptB_m1 = -1;
+  // stream the panels per batch when the whole set, with the operand batch
+  // budget, chi and the Green's functions, does not fit in free memory
+  {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double need = (double)slices * rows * kmax * 2 + ctx->batch_bytes +
+                        3.0 * ctx->nri * (double)ctx->nri * 8 + 5.0 * ctx->nao * (double)ctx->nao * 8 + 2e9;
+    ctx->pt_stream = ctx->panel_stream || need > (double)free_b;
+  }
+  if (ctx->pt_stream) {
+    double pt_scale = 1.0;
+    int rc;
+    if (f16) {
+      double *st2, h[4] = {0, 0, 0, 0};
+      if ((rc = wsT(ctx, "pt_absmax", 4, &st2))) return rc;
+      const long long n = ctx->n_elems, nrow = n / 1024;
+      if (ctx->d_t3f) {
+        gw::launch_absmax_f32(ctx->d_t3f, n, st2, ctx->stream);
+        GW_TRY(cudaMemsetAsync(st2 + 2, 0, 2 * sizeof(double), ctx->stream));
+      } else {
+        gw::launch_absmax_rowsum(ctx->d_t3, 1024, (int)nrow, 1024, st2, ctx->stream);
+        gw::launch_absmax_rowsum(ctx->d_t3 + nrow * 1024, 1024, n > nrow * 1024 ? 1 : 0,
+                                 (int)(n - nrow * 1024), st2 + 2, ctx->stream);
+      }
+      GW_CHECK_LAUNCH();
+      GW_TRY(cudaMemcpyAsync(h, st2, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+      GW_TRY(cudaStreamSynchronize(ctx->stream));
+      ctx->t_absmax = std::max(h[0], h[2]);
+      pt_scale = gw::pow2_scale(ctx->t_absmax);
+    }
+    ctx->pt_rows = 0;
+    ctx->pt_kmax = kmax;
+    ctx->pt_slices = slices;
+    ctx->pt_f16 = f16;
+    ctx->pt_scale = pt_scale;
+    ctx->pt_thr = ctx->plan_thr;
+    ctx->pt_ok = true;
+    return GW_OK;
+  }
   // rows of each kept block in the two panels it lands in: (pw of its first
   // RI function, s' = 0)
   const std::vector<int>& kept = ctx->plan_kept;
@@ -883,6 +942,72 @@ int ensure_pt(gw_ctx* ctx, int slices, int f16) {
   ctx->pt_scale = pt_scale;
   ctx->pt_thr = ctx->plan_thr;
   ctx->pt_ok = true;
+  return GW_OK;
+}
+
+// Streamed split panels of the atoms in [a0, a1) into the named region: rows
+// per atom in that order (row0[atom], -1 for atoms without a panel), the
+// region zeroed and scattered from the kept blocks in which the atom is an
+// owner.  *rows_out = the region's rows.
+int build_pt_region(gw_ctx* ctx, const char* name, int a0, int a1, void** buf, long long* rows_out,
+                    std::vector<int>& row0) {
+  const int slices = ctx->pt_slices, kmax = ctx->pt_kmax;
+  row0.assign(ctx->n_at, -1);
+  long long rows = 0;
+  for (int s = a0; s < a1; ++s) {
+    const gw::PanelTaskTC& t = ctx->pt_tasks[s];
+    if (t.K == 0) continue;
+    row0[s] = (int)rows;
+    rows += (t.N + 127) / 128 * 128;
+  }
+  *rows_out = rows;
+  const size_t bytes = std::max<size_t>((size_t)slices * rows * kmax * 2, 16);
+  int rc;
+  if ((rc = ws(ctx, name, bytes, buf))) return rc;
+  GW_TRY(cudaMemsetAsync(*buf, 0, bytes, ctx->stream));
+  // one entry per (kept block, owner side in the range)
+  std::vector<int> ent_blk, ent_kB, ent_kA;
+  std::vector<long long> ent_rowB, ent_rowA;
+  for (int s = a0; s < a1; ++s) {
+    if (row0[s] < 0) continue;
+    const gw::PanelTaskTC& t = ctx->pt_tasks[s];
+    for (int e = ctx->plan_atom_off[s]; e < ctx->plan_atom_off[s + 1]; ++e) {
+      const int i = ctx->plan_atom_blk[e];
+      const int b = ctx->plan_kept[i];
+      const int B = ctx->blk[3 * b + 1], p = ctx->blk[3 * b + 2];
+      const long long r = row0[s] + (long long)(ctx->ri_off[p] - t.p0) * t.nsig;
+      ent_blk.push_back(b);
+      if (B == s) {
+        ent_rowB.push_back(r);
+        ent_kB.push_back(ctx->plan_kB[i]);
+        ent_rowA.push_back(-1);
+        ent_kA.push_back(0);
+      } else {
+        ent_rowB.push_back(-1);
+        ent_kB.push_back(0);
+        ent_rowA.push_back(r);
+        ent_kA.push_back(ctx->plan_kA[i]);
+      }
+    }
+  }
+  int *d_blk, *d_kB, *d_kA, *d_nao, *d_nri;
+  long long *d_rowB, *d_rowA;
+  if ((rc = upload(ctx, "ptr_blk", ent_blk, &d_blk)) || (rc = upload(ctx, "ptr_kB", ent_kB, &d_kB)) ||
+      (rc = upload(ctx, "ptr_kA", ent_kA, &d_kA)) || (rc = upload(ctx, "ptr_rowB", ent_rowB, &d_rowB)) ||
+      (rc = upload(ctx, "ptr_rowA", ent_rowA, &d_rowA)) || (rc = upload(ctx, "n_ao", ctx->n_ao, &d_nao)) ||
+      (rc = upload(ctx, "n_ri", ctx->n_ri, &d_nri)))
+    return rc;
+  if (ctx->d_t3f)
+    gw::launch_pt_scatter_f32(ctx->d_t3f, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_blk,
+                              (long long)ent_blk.size(), d_rowB, d_kB, d_rowA, d_kA, kmax, slices,
+                              rows * kmax, ctx->pt_f16, ctx->pt_scale, *buf, ctx->stream);
+  else
+    gw::launch_pt_scatter(ctx->d_t3, ctx->d_blk, ctx->d_blk_off, d_nao, d_nri, d_blk,
+                          (long long)ent_blk.size(), d_rowB, d_kB, d_rowA, d_kA, kmax, slices, rows * kmax,
+                          ctx->pt_f16, ctx->pt_scale, *buf, ctx->stream);
+  GW_CHECK_LAUNCH();
+  // the host tables are read by the copies above before they go out of scope
+  GW_TRY(cudaStreamSynchronize(ctx->stream));
   return GW_OK;
 }
 
@@ -993,9 +1118,31 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   GW_TRY(cudaMemsetAsync(by2, 0, (size_t)ns * nmc * nqa * sizeof(float), ctx->stream));
   int* d_err;  // zeroed once per tau point by gw_chi_tau
   if ((rc = wsT(ctx, "tc_err", 1, &d_err))) return rc;
-  CUtensorMap mp;
-  if (gw::make_slice_map(&mp, ctx->d_pt, kmax, ctx->pt_rows, slices, tile, f16))
-    return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
+  // split panels: the resident set for both steps, or streamed regions (A:
+  // the batch's owners, rebuilt per batch; B: the chunk's atoms, rebuilt when
+  // the chunk changes)
+  CUtensorMap mpA, mpB;
+  std::vector<int> row0A;
+  if (ctx->pt_stream) {
+    void* bufA;
+    long long rowsA = 0;
+    if ((rc = build_pt_region(ctx, "ptA", b.s0, b.s1, &bufA, &rowsA, row0A))) return rc;
+    if (ctx->ptB_m0 != b.m0 || ctx->ptB_m1 != b.m1) {
+      ctx->ptB_m0 = ctx->ptB_m1 = -1;
+      if ((rc = build_pt_region(ctx, "ptB", b.m0, b.m1, &ctx->d_ptB_region, &ctx->ptB_rows, ctx->ptB_row0)))
+        return rc;
+      ctx->ptB_m0 = b.m0;
+      ctx->ptB_m1 = b.m1;
+    }
+    if (gw::make_slice_map(&mpA, bufA, kmax, std::max<long long>(rowsA, 1), slices, tile, f16) ||
+        gw::make_slice_map(&mpB, ctx->d_ptB_region, kmax, std::max<long long>(ctx->ptB_rows, 1), slices, tile,
+                           f16))
+      return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the streamed panels");
+  } else {
+    if (gw::make_slice_map(&mpA, ctx->d_pt, kmax, ctx->pt_rows, slices, tile, f16))
+      return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panels");
+    mpB = mpA;
+  }
   double issued = 0.0;
   cudaEvent_t ea0, ea1;
   if ((rc = c_event_pair(ctx, 2 * batch_idx + 1, &ea0, &ea1))) return rc;
@@ -1016,6 +1163,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     for (int s = b.s0; s < b.s1; ++s) {
       gw::PanelTaskTC t = ctx->pt_tasks[s];
       if (t.K == 0) continue;
+      if (ctx->pt_stream) t.p_row0 = row0A[s];
       t.g_row0 = (int)ta.size() * rows_a;
       t.seg = b.seg[s - b.s0];
       t.s_local = s - b.s0;
@@ -1052,12 +1200,12 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (gw::make_slice_map(&mg, gg, kmax, (long long)ta.size() * rows_a, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step A)");
       const int lrc =
-          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
+          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mpA, d_tiles,
                                               (int)tiles.size(), d_ta, 0, xs, (long long)prow * Kb, Kb,
                                               b.P0, b.Lc, 0, b.s0, nullptr, bx2, ctx->d_atom_of_ri,
                                               ctx->d_atom_of_ao, ctx->d_ao_off, ctx->d_ri_off, d_nao_a,
                                               npa, pa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream)
-                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mp, d_tiles,
+                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_go * s_t)), (float)s_x, mg, mpA, d_tiles,
                                        (int)tiles.size(), d_ta, 0, b.nmu, xs,
                                        (long long)prow * Kb, Kb, b.P0, nullptr, nullptr, nullptr, bx2,
                                        ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, npa,
@@ -1085,6 +1233,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     for (int m = b.m0; m < b.m1; ++m) {
       gw::PanelTaskTC t = ctx->pt_tasks[m];
       if (t.K == 0) continue;
+      if (ctx->pt_stream) t.p_row0 = ctx->ptB_row0[m];
       t.aom -= b.mu0;  // chunk-local first AO of the panel's owner
       t.g_row0 = (int)tb.size() * rows_b;
       if (staged) {
@@ -1132,12 +1281,12 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
       const int lrc =
-          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
+          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mpB, d_tiles,
                                               (int)tiles.size(), d_tb, 1, ys, (long long)qrow * Kb, Kb,
                                               b.Q0, b.Lc, r0, b.s0, d_rowbase, by2, ctx->d_atom_of_ri,
                                               ctx->d_atom_of_ao, ctx->d_ao_off, ctx->d_ri_off, d_nao_a,
                                               nqa, qa0, b.mu0, b.m0, nmc, ctx->flush_k, d_err, ctx->stream)
-                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mp, d_tiles,
+                 : gw::launch_panel_tc(slices, f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mpB, d_tiles,
                                        (int)tiles.size(), d_tb, 1, R, ys,
                                        (long long)qrow * Kb, Kb, b.Q0, d_rowbase, d_rowmul, d_rowsl, by2,
                                        ctx->d_atom_of_ri, ctx->d_atom_of_ao, ctx->d_ao_off, n_at, nqa,
@@ -1766,6 +1915,12 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
   if (!strcmp(key, "flush_k")) {
     if (!(value >= 16 && value <= (1 << 30))) return fail(ctx, GW_ERR_INVALID_ARG, "flush_k must be in [16, 2^30]");
     ctx->flush_k = (int)value;
+    return GW_OK;
+  }
+  if (!strcmp(key, "panel_stream")) {
+    if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "panel_stream must be 0 or 1");
+    ctx->panel_stream = (int)value;
+    ctx->pt_ok = false;
     return GW_OK;
   }
   if (!strcmp(key, "tensor_fp32")) {

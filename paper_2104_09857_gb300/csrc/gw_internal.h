@@ -199,6 +199,16 @@ struct gw_ctx {
   long long pt_rows = 0;
   int pt_kmax = 0;
   std::vector<gw::PanelTaskTC> pt_tasks;  // per atom (K == 0: none)
+  // streamed split panels: when the whole set does not fit, step A builds
+  // the panels of a batch's owners and step B those of a chunk's atoms, each
+  // in a region of its own, from the stored blocks
+  bool pt_stream = false;
+  int panel_stream = 0;            // option: 1 always stream
+  int ptB_m0 = -1, ptB_m1 = -1;    // chunk whose panels region B holds
+  long long ptB_rows = 0;
+  void* d_ptB_region = nullptr;    // region B's buffer (a named work buffer)
+  std::vector<int> ptB_row0;       // per atom: first row in region B (-1: absent)
+  std::vector<int> plan_atom_off, plan_atom_blk;  // per atom: indices into plan_kept of its blocks
   // per RI row q: the owner atoms whose panel windows cover q, [ycov_lo,
   // ycov_hi] (lo < 0: none); valid when they are contiguous for every q
   // tensor-core batches of the current tau point whose flop counts and

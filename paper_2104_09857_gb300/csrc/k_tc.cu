@@ -1125,8 +1125,9 @@ __global__ void k_pt_scatter(const T* __restrict__ t3, const int* __restrict__ b
     const int na = n_ao[A], nb = n_ao[B], np = n_ri[p];
     const T* x = t3 + off[b];
     const long long n = static_cast<long long>(na) * nb * np;
-    // panel B: i = (P' nb + sigma') na + lambda'
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    // panel B: i = (P' nb + sigma') na + lambda' (a row below 0: the side is
+    // not built in this call)
+    for (long long i = threadIdx.x; rowB[kb] >= 0 && i < n; i += blockDim.x) {
       const int al = static_cast<int>(i % na);
       const long long r = i / na;  // P' nb + sigma'
       const int be = static_cast<int>(r % nb), pl = static_cast<int>(r / nb);
@@ -1134,7 +1135,7 @@ __global__ void k_pt_scatter(const T* __restrict__ t3, const int* __restrict__ b
       const long long dst = (rowB[kb] + r) * kmax + kB[kb] + al;
       for (int s = 0; s < slices; ++s) out[s * slice_elems + dst] = take_slice(v, f16 != 0);
     }
-    if (A == B) continue;
+    if (A == B || rowA[kb] < 0) continue;
     // panel A: i = (P' na + lambda') nb + sigma'
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
       const int be = static_cast<int>(i % nb);

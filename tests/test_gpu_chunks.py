@@ -173,3 +173,18 @@ def test_learned_screening_with_chunks(lib):
         st = ctx.stats()
     assert st["n_batches"] > 1 and st["tasks_seen"] > 0
     _check(got, ref, 1e-6)
+
+
+@pytest.mark.parametrize("chunk", [0, 7])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_streamed_panels_give_the_same_chi(lib, chunk, fp32):
+    """Split panels streamed per batch (the owners' for step A, the chunk's for
+    step B, built from the stored blocks) hold the same values as the resident
+    set: with whole-tile step-C units chi is bitwise the same."""
+    case = make_case("ribbon28", n_tau=2)
+    opts = {"c_split_k": 0, "mu_chunk_atoms": chunk, "batch_atoms": 5, "tensor_fp32": fp32}
+    a, sa = _run(lib, case, "fp16x3", case.thr, dict(opts, panel_stream=1))
+    b, sb = _run(lib, case, "fp16x3", case.thr, opts)
+    assert np.array_equal(a, b)
+    assert sa["flops_useful"] == sb["flops_useful"]
+    _check(a, oc.chi_dense(case), 1e-6)

@@ -677,6 +677,77 @@ def run_sigma_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned_cluster(args):
+    """Learned screening on the 500-atom disordered cluster (thr 1e-9): the
+    norm-bound screen against the learned one on the timed form at a few tau
+    points, with skipped tasks, time, and the error of both against the FP64
+    block oracle on sampled diagonal blocks.  The tensor is kept in FP32 on the
+    device and the split panels are streamed (the whole set would need about
+    405 GB)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2104_09857_gb300 import Context, _lib
+    from synth import make_case
+
+    prec = args.precision
+    t0 = time.perf_counter()
+    case = make_case("cluster500")
+    t_gen = time.perf_counter() - t0
+    params, margin, info = _train_screen(Context, 0, case.thr, prec)
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream)
+    ctx.set_option("tensor_fp32", 1)
+    ctx.set_option("batch_bytes", args.batch_bytes if args.batch_bytes > 0 else 20e9)
+    ctx.load_case(case)
+    _lib.gw_mlp_set_params(ctx.ctx, params)
+    ctx.set_option("mlp_margin", margin)
+    nri = ctx.nri
+    out = torch.empty((1, nri, nri), dtype=torch.float64, device="cuda:0")
+    ri = np.concatenate([[0], np.cumsum(case.system.n_ri)])
+    taus = [int(t) for t in args.cluster_taus.split(",")]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    from oracle import chi as oc
+
+    bo = oc.BlockOracle(case)
+    perm = np.random.default_rng(20210420).permutation(case.system.n_atoms)
+    rows = []
+    for j in taus:
+        a = int(perm[j])
+        rec = {"tau_index": j, "tau": float(case.tau[j]), "atom": a}
+        got = {}
+        for name, scr in (("norm_bound", _lib.GW_SCREEN_BOUND), ("learned", _lib.GW_SCREEN_MLP)):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.chi_tau(case.thr, prec, j, 1, out=out, screening=scr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            got[name] = _diag_blocks(out[0], ri, [a])
+            rec[name] = {"ms": e0.elapsed_time(e1), "useful_tflops": st["flops_useful"] / e0.elapsed_time(e1) / 1e9,
+                         "flops_issued": st["flops_issued"], "tasks_seen": st["tasks_seen"],
+                         "tasks_skipped": st["tasks_skipped"], "n_batches": st["n_batches"]}
+        ref = bo.block(j, a, a, {})
+        for name in got:
+            rel, el = _block_errors(got[name], [ref])
+            rec[name].update({"rel_frobenius": rel, "rel_element": el})
+        rel, el = _block_errors(got["learned"], got["norm_bound"])
+        rec["learned_vs_norm_bound"] = {"rel_frobenius": rel, "rel_element": el}
+        rows.append(rec)
+    ctx.close()
+    line = {"metric": "learned vs norm-bound screening of chi(i tau), 500-atom disordered cluster",
+            "unit": "ms per tau point", "n_gpus": 1, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"cluster-500 ({case.system.nao_total} AO / {case.system.nri_total} RI, "
+                                   "0.1 atoms/A^3, thr 1e-9)", "tensor": "FP32 on the device",
+                       "panels": "streamed per batch"},
+            "per_tau": rows, "training": info, "setup_s": t_gen}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -707,7 +778,12 @@ def main():
                     help="device bytes for one batch's X and Y operands (0: the library default)")
     ap.add_argument("--sigma-check", type=int, default=6,
                     help="batched self-energy workload: molecules checked against the oracle")
+    ap.add_argument("--cluster-taus", default="1,3",
+                    help="500-atom cluster workload: tau indices (of 6) timed and checked")
     args = ap.parse_args()
+    if args.workload == "cluster500":
+        run_learned_cluster(args)
+        return
     if args.workload == "molecules64":
         run_sigma_batch(args)
         return

@@ -175,6 +175,9 @@ CASES = {
     "ribbon120": (lambda: armchair_ribbon(10), 6, 1e-9, 20210427),
     # 144.5 cells: 1156 C + 576 H = 1732 atoms, 17 908 AO / 41 592 RI
     "ribbon1734": (lambda: armchair_ribbon(144.5), 30, 1e-9, 20210423),
+    # 500 atoms uniform in a 17.1 A cube (0.1 atoms/A^3, >= 1.0 A apart), C with
+    # probability 2/3: 5220 AO / 12 120 RI
+    "cluster500": (lambda: random_cluster(500, 0.1, 1.0, 20210424), 6, 1e-9, 20210424),
     "chain_HH": (lambda: tiny_chain("HH", 1.0), 3, 0.0, 6),
     "chain_CH": (lambda: tiny_chain("CH"), 3, 0.0, 7),
     "chain_HCH": (lambda: tiny_chain("HCH"), 3, 0.0, 8),

@@ -695,36 +695,44 @@ struct PanelStagedJob {
     h0 = take_slice(v, f);
     h1 = take_slice(v, f);
   }
-  // Sum of squares over the staged rectangle rows [r0, r1) x cols [c0, c1),
-  // added into norm2[key] by lane 0 (all 32 lanes call).
-  __device__ static void rect_norm(const float* tile, int r0, int r1, int c0, int c1, int lane,
-                                   float* norm2, int key) {
-    const int w = c1 - c0, n = (r1 - r0) * w;
-    float ss = 0.f;
-    for (int i = lane; i < n; i += 32) {
-      const float v = tile[(r0 + i / w) * kTilePitch + c0 + i % w];
-      ss += v * v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0 && ss != 0.f) atomicAdd(norm2 + key, ss);
-  }
-
+  // The tile is staged in the output's own order, so that every output run is
+  // a contiguous run of the staging buffer:
+  //   mode 0: [pw run g][mu column c][s'],  position g 128 nsig + c nsig + s'
+  //   mode 1: per owner s (first tile row r_s): [column c][sigma' of s],
+  //           position ng nm r_s + c n(s) + sigma'  (c = g nm + mu', so the
+  //           run of (s, pw g) starts at ng nm r_s + g nm n(s))
   __device__ bool write_staged(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
                                EpiCtx& ep) const {
-    float* tile = reinterpret_cast<float*>(ep.staging);
+    float* stg = reinterpret_cast<float*>(ep.staging);
+    const PanelTaskTC& tk = tasks[T.task];
     // the previous tile has been written out by every epilogue warp
     if (ep.tile_no > 0 && !mbar_wait(ep.freed, static_cast<uint32_t>(ep.tile_no - 1) & 1u, ep.abort))
       return false;
-    {
-      float* row = tile + (quad * 32 + lane) * kTilePitch + c0;
+    const int r = quad * 32 + lane;  // this thread's tile row
+    if (mode == 0) {
+      const int nsig = tk.nsig;
+      if (r < T.rv) {
+        const int g = r / nsig, sp = r - g * nsig;
+        float* base = stg + g * kTileN * nsig + sp + c0 * nsig;
 #pragma unroll
-      for (int j = 0; j < kEpiCols; ++j) row[j] = acc[j] * unscale;
+        for (int j = 0; j < kEpiCols; ++j) base[j * nsig] = acc[j] * unscale;
+      }
+    } else {
+      const int nm = n_ao[tk.owner];
+      const int ng = T.cv / nm;
+      if (r < T.rv) {
+        const int a = row_ao0 + T.ra + r;
+        const int s = atom_of_ao[a];
+        const int nsg = n_ao[s], sp = a - ao_off[s];
+        float* base = stg + ng * nm * (r - sp) + sp + c0 * nsg;
+#pragma unroll
+        for (int j = 0; j < kEpiCols; ++j)
+          if (c0 + j < T.cv) base[j * nsg] = acc[j] * unscale;
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(ep.staged);
     if (!mbar_wait(ep.staged, static_cast<uint32_t>(ep.tile_no) & 1u, ep.abort)) return false;
-    const PanelTaskTC& tk = tasks[T.task];
     const bool f = f16 != 0;
     const int tid = ep.warp * 32 + lane;
     constexpr int kThr = kEpiWarps * 32;
@@ -733,37 +741,31 @@ struct PanelStagedJob {
       const int ng = T.rv / nsig;               // pw runs in the tile
       const int pw0 = T.ra / nsig;
       const int mu0 = T.rb;                     // chunk-local
-      const int ncol = min(kTileN, Lc - mu0);   // X columns written (zeros past cv)
+      const int ncol = min(kTileN, Lc - mu0);   // X columns written (exact zeros past cv)
       const int units = ncol * nsig / 8;        // 8-element vectors per run
-      for (int u = tid; u < ng * units; u += kThr) {
-        const int g = u / units;
-        const int e0 = (u - g * units) * 8;
-        int mu = e0 / nsig, sp = e0 - mu * nsig;
-        uint32_t w0[4], w1[4];
+      for (int g = 0; g < ng; ++g) {
+        const float* run = stg + g * kTileN * nsig;
+        uint16_t* o0 = out + static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk + tk.seg +
+                       static_cast<long long>(mu0) * nsig;
+        for (int u = tid; u < units; u += kThr) {
+          const float4 va = *reinterpret_cast<const float4*>(run + 8 * u);
+          const float4 vb = *reinterpret_cast<const float4*>(run + 8 * u + 4);
+          const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+          uint32_t w0[4], w1[4];
 #pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          uint16_t a0, a1, b0, b1;
-          const float va = mu < T.cv ? tile[(g * nsig + sp) * kTilePitch + mu] * out_scale : 0.f;
-          if (++sp == nsig) {
-            sp = 0;
-            ++mu;
+          for (int k = 0; k < 8; k += 2) {
+            uint16_t a0, a1, b0, b1;
+            pack_slices(v[k] * out_scale, f, a0, a1);
+            pack_slices(v[k + 1] * out_scale, f, b0, b1);
+            w0[k / 2] = static_cast<uint32_t>(a0) | (static_cast<uint32_t>(b0) << 16);
+            w1[k / 2] = static_cast<uint32_t>(a1) | (static_cast<uint32_t>(b1) << 16);
           }
-          const float vb = mu < T.cv ? tile[(g * nsig + sp) * kTilePitch + mu] * out_scale : 0.f;
-          if (++sp == nsig) {
-            sp = 0;
-            ++mu;
-          }
-          pack_slices(va, f, a0, a1);
-          pack_slices(vb, f, b0, b1);
-          w0[k / 2] = static_cast<uint32_t>(a0) | (static_cast<uint32_t>(b0) << 16);
-          w1[k / 2] = static_cast<uint32_t>(a1) | (static_cast<uint32_t>(b1) << 16);
+          *reinterpret_cast<uint4*>(o0 + 8 * u) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+          *reinterpret_cast<uint4*>(o0 + slice_elems + 8 * u) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
         }
-        const long long dst = static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk + tk.seg +
-                              static_cast<long long>(mu0) * nsig + e0;
-        *reinterpret_cast<uint4*>(out + dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *reinterpret_cast<uint4*>(out + slice_elems + dst) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
       }
-      // norms: rectangles (RI atom of the rows) x (mu-atom of the columns)
+      // norms: rectangles (RI atom of the pw runs) x (mu-atom of the columns);
+      // a rectangle is, in each of its runs, one contiguous segment
       const int pf = atom_of_ri[tk.p0 + pw0], pl = atom_of_ri[tk.p0 + pw0 + ng - 1];
       const int mf = atom_of_ao[mu_base + mu0], ml = atom_of_ao[mu_base + mu0 + T.cv - 1];
       const int np = pl - pf + 1;
@@ -771,8 +773,15 @@ struct PanelStagedJob {
         const int m = mf + k / np, pa = pf + k % np;
         const int g0 = max(0, ri_off[pa] - tk.p0 - pw0), g1 = min(ng, ri_off[pa + 1] - tk.p0 - pw0);
         const int cc0 = max(0, ao_off[m] - mu_base - mu0), cc1 = min(T.cv, ao_off[m + 1] - mu_base - mu0);
-        rect_norm(tile, g0 * nsig, g1 * nsig, cc0, cc1, lane, norm2,
-                  (tk.s_local * nmc + (m - m_base)) * npa + (pa - pa0));
+        float ss = 0.f;
+        for (int g = g0; g < g1; ++g) {
+          const float* seg = stg + g * kTileN * nsig + cc0 * nsig;
+          for (int i = lane; i < (cc1 - cc0) * nsig; i += 32) ss += seg[i] * seg[i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0 && ss != 0.f)
+          atomicAdd(norm2 + (tk.s_local * nmc + (m - m_base)) * npa + (pa - pa0), ss);
       }
     } else {
       const int nm = n_ao[tk.owner];            // mu' per pw run
@@ -780,18 +789,18 @@ struct PanelStagedJob {
       const int pw0 = T.rb / nm;
       const int sf = atom_of_ao[row_ao0 + T.ra], sl = atom_of_ao[row_ao0 + T.ra + T.rv - 1];
       const int ns = sl - sf + 1;
-      // one region (owner s, pw) per warp in turn: write and norm together
+      // one region (owner s, pw run g) per warp in turn: write and norm together
       for (int k = ep.warp; k < ns * ng; k += kEpiWarps) {
         const int s = sf + k / ng, g = k % ng;
         const int nsg = n_ao[s];
-        const int r0 = ao_off[s] - row_ao0 - T.ra;   // staged row of sigma' = 0
+        const int rs = ao_off[s] - row_ao0 - T.ra;   // tile row of sigma' = 0
+        const float* run = stg + ng * nm * rs + g * nm * nsg;
         const long long dst = static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk +
                               rowbase[ao_off[s] - row_ao0] + static_cast<long long>(tk.aom) * nsg;
         const int len = nm * nsg;
         float ss = 0.f;
         for (int e = lane; e < len; e += 32) {
-          const int mp = e / nsg, sp = e - mp * nsg;
-          const float v = tile[(r0 + sp) * kTilePitch + g * nm + mp];
+          const float v = run[e];
           ss += v * v;
           uint16_t h0, h1;
           pack_slices(v * out_scale, f, h0, h1);

@@ -267,21 +267,29 @@ def _roof(flops, seconds, prec, peaks, peak_src, kernel, traffic, alu=None):
             "peak_note": note}
 
 
-def _traffic(prec):
-    """DRAM bytes per launch of the tensor-core kernels from the committed ncu
-    summary, if it was taken on the current kernel source and form."""
+def _traffic(prec, step_flops):
+    """DRAM bytes per launch of the two tensor-core kernels on the bench
+    workload, from the one-pass ncu counters of a small case of the same
+    kernels (profiles/traffic_fp16x3_ribbon120.json), scaled to a full launch
+    by the useful flops each launch processes: X and Y written, panels and G
+    read, and step C's operand reads all grow with that work.  Empty when the
+    record was taken on another kernel source or form."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "traffic_fp16x3_ribbon298.json")
+    path = os.path.join(ROOT, "profiles", "traffic_fp16x3_ribbon120.json")
     src = os.path.join(ROOT, "paper_2104_09857_gb300", "csrc", "k_tc.cu")
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
         return {}
-    if rec.get("k_tc_sha256") != sha or rec.get("form") != prec:
+    if rec.get("k_tc_sha256") != sha or rec.get("form") != prec or not step_flops:
         return {}
-    return {"ab": rec.get("panel_job_bytes_per_launch"), "c": rec.get("chi_job_bytes_per_launch")}
+    nb = max(1.0, step_flops["batches"])
+    ab = (rec["step_a_bytes"] / rec["step_a_flops"] * step_flops["a"] / nb +
+          rec["step_b_bytes"] / rec["step_b_flops"] * step_flops["b"] / nb) / 2.0
+    c = rec["step_c_bytes"] / rec["step_c_flops"] * step_flops["c"] / nb
+    return {"ab": ab, "c": c}
 
 
 def _block_errors(got_blocks, ref_blocks):
@@ -446,8 +454,9 @@ def run_ours(args):
     # rooflines of the two tensor-core kernels: steps A/B (k_tc_persistent
     # PanelJob, two launches per batch) and step C (ChiJob, one per batch);
     # "roofline" is the one that takes more time
-    traffic = _traffic(prec)
     nb = max(1, agg["n_batches"])
+    traffic = _traffic(prec, {"a": agg["flops_a"], "b": agg["flops_b"], "c": agg["flops_c"],
+                              "batches": float(nb)})
     roof_ab = _roof(agg["flops_a"] + agg["flops_b"], agg["ms_step_ab"] / 1e3, prec, peaks, peak_src,
                     "steps A/B (panel job; time includes the two G gathers)", traffic.get("ab"), alu)
     roof_c = _roof(agg["flops_c"], agg["ms_step_c_kernel"] / 1e3, prec, peaks, peak_src,
@@ -528,8 +537,10 @@ def run_ours(args):
         forms["useful_flops_oracle"] = flops_oracle
         result["forms"] = forms
         # per-tau parity of the timed form: one diagonal block per tau point
-        result["parity"], oracle_blocks = _per_tau_parity(
-            case, lambda j: step(j, prec), out, ri, prec, list(range(min(args.parity_taus, n_tau))))
+        oracle_blocks = {}
+        if args.parity_taus > 0:
+            result["parity"], oracle_blocks = _per_tau_parity(
+                case, lambda j: step(j, prec), out, ri, prec, list(range(min(args.parity_taus, n_tau))))
         # learned screening at the bench threshold: time, skipped tasks,
         # per-tau error on the same oracle blocks
         if args.learned:

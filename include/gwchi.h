@@ -459,9 +459,13 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *                  keeps Y over every RI function, several give each chunk
  *                  the RI window of its atoms' 3c blocks)
  *   "flush_k"      split forms: reduction elements between drains of the
- *                  tensor cores' main FP32 accumulator (rounded down to a
+ *                  tensor cores' FP32 accumulator (rounded down to a
  *                  multiple of 16, default 64; each 16-element MMA step of the
- *                  accumulation loses about half an ulp toward zero)
+ *                  accumulation loses about half an ulp of the running sum
+ *                  toward zero; within one 64-element step of a drain
+ *                  interval the smaller slice products enter first, so an
+ *                  interval of at most 64 costs the main product's roundings
+ *                  only)
  *   "c_split_k"    split forms: step-C work units cover about this many
  *                  reduction elements of one 128 x 128 chi tile and add into
  *                  chi with FP64 atomics, so the summation order (and the

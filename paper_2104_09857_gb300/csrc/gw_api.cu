@@ -1223,20 +1223,30 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     std::vector<gw::PanelTaskTC> tb;
     std::vector<int4> tiles;
     // staged: batch rows in groups of whole owner atoms, at most one tile each
-    std::vector<std::pair<int, int>> groups;
-    if (staged)
+    std::vector<std::pair<int, int>> groups, group_atoms;
+    bool staged_b = staged;
+    if (staged_b)
       for (int s = b.s0; s < b.s1;) {
-        const int g0 = ctx->ao_off[s] - r0;
+        const int g0 = ctx->ao_off[s] - r0, a0 = s;
         while (s < b.s1 && ctx->ao_off[s + 1] - r0 - g0 <= tile) ++s;
         groups.push_back({g0, ctx->ao_off[s] - r0 - g0});
+        group_atoms.push_back({a0, s});
       }
+    // every (owner, row group) tile must fit in the staging area
+    for (int m = b.m0; m < b.m1 && staged_b; ++m)
+      if (ctx->pt_tasks[m].K > 0)
+        for (const auto& ga : group_atoms)
+          if (!gw::staged_fits_mode1(ctx->n_ao[m], ctx->n_ao.data() + ga.first, ga.second - ga.first)) {
+            staged_b = false;
+            break;
+          }
     for (int m = b.m0; m < b.m1; ++m) {
       gw::PanelTaskTC t = ctx->pt_tasks[m];
       if (t.K == 0) continue;
       if (ctx->pt_stream) t.p_row0 = ctx->ptB_row0[m];
       t.aom -= b.mu0;  // chunk-local first AO of the panel's owner
       t.g_row0 = (int)tb.size() * rows_b;
-      if (staged) {
+      if (staged_b) {
         const int meff = tile / t.nsig * t.nsig;  // whole runs of the owner's functions
         int ntn = 0;
         for (int rb = 0; rb < t.N; rb += meff, ++ntn)
@@ -1281,7 +1291,7 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (gw::make_slice_map(&mg, gg, kmax, (long long)tb.size() * rows_b, slices, tile, f16))
         return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed for G (step B)");
       const int lrc =
-          staged ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mpB, d_tiles,
+          staged_b ? gw::launch_panel_tc_staged(f16, (float)(1.0 / (s_gv * s_t)), (float)s_y, mg, mpB, d_tiles,
                                               (int)tiles.size(), d_tb, 1, ys, (long long)qrow * Kb, Kb,
                                               b.Q0, b.Lc, r0, b.s0, d_rowbase, by2, ctx->d_atom_of_ri,
                                               ctx->d_atom_of_ao, ctx->d_ao_off, ctx->d_ri_off, d_nao_a,
@@ -1351,7 +1361,8 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   if ((rc = upload(ctx, "n_ri_b", ctx->n_ri, &d_nri))) return rc;
   gw::launch_count_c(bx, by, ns, b.m0, nmc, pa0, npa, qa0, nqa, d_nri, d_nao, b.s0, d_fc, ctx->stream);
   GW_CHECK_LAUNCH();
-  ctx->stats.kernel_launches += 4;
+  // two block filters of two kernels each, the task lists and the count
+  ctx->stats.kernel_launches += 6;
   double fc_scale = 1.0;
   if (ctx->mlp_mode) {
     gw::MlpBatch mb{};

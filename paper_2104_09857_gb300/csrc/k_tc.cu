@@ -24,17 +24,21 @@
 //   warps 2..17 epilogue (4 lane quadrants x 4 groups of 32 columns): the
 //               TMEM accumulators are read into an FP32
 //               register sum per element; the job writes it out at the end
-//               of a tile (ChiJob also every kWriteK reduction elements).
+//               of a tile (ChiJob also every kWriteK reduction elements), or
+//               stages it in shared memory and copies it out from there
 // The tensor cores' FP32 accumulation rounds each MMA step's result toward
-// zero (measured: a bias of about half an ulp per step, so the relative
-// error grows with the number of steps between drains), so the main slice
-// product (0, 0) accumulates alone and is drained every few MMA steps
-// (flush_k reduction elements); the small products, 2^-8 of it or less,
-// share a second accumulator drained every kSmallK elements.  TMEM: three
-// main accumulators of 128 columns (the MMA may run two drains ahead of the
-// epilogue) and one small accumulator of 128 columns.  Every mbarrier wait is bounded; on time-out the CTA raises the
-// error flag, waits (bounded) for the copies and products it issued, frees
-// its TMEM and returns.
+// zero (measured: a bias of about half an ulp of the running sum per step,
+// so the relative error grows with the number of steps between drains), so
+// the accumulator is drained every few MMA steps (flush_k reduction
+// elements).  Within one drain interval the small slice products (2^-8 of
+// the main one or less) are issued first, while the sum is small: their
+// roundings fall below the main product's ulp, and the interval costs the
+// main product's few roundings only.  TMEM: four accumulators of 128 columns,
+// used in turn (the MMA may run three drains ahead of the epilogue, and a
+// tile starts without waiting for the previous one's last drain).  Every
+// mbarrier wait is bounded; on time-out the CTA raises the error flag, waits
+// (bounded) for the copies and products it issued, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -55,13 +59,10 @@ constexpr int kTileN = 128;
 constexpr int kStageK = 64;   // bf16 elements per K step: one 128-byte swizzled row
 constexpr int kMmaK = 16;
 constexpr int kEpiWarps = 16;                 // 4 TMEM lane quadrants x 4 column groups
-constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kEpiCols = kTileN / 4;          // accumulator columns per epilogue warp
-constexpr int kSmallK = 2048;  // reduction elements between drains of the small accumulator
 constexpr int kWriteK = 2048;  // reduction elements between ChiJob write-outs (one per split-K unit)
 constexpr int kTmemCols = 512;
-constexpr int kMainBufs = 3;   // main accumulators: TMEM columns [0, 384)
-constexpr uint32_t kSmallCol = 384;  // the small accumulator: columns [384, 512)
+constexpr int kAccBufs = 4;   // accumulators: TMEM columns [128 b, 128 b + 128)
 constexpr uint32_t kSuspendNs = 20000;            // longest suspension of one try_wait
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -121,6 +122,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16) from shared to global memory, both
+// addresses 16-byte aligned, as a bulk async-group of the issuing thread.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"(smem_u32(ssrc)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's bulk groups have been read
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// this thread's bulk groups have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's shared-memory writes before later async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -217,11 +236,10 @@ __device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
   }
 }
 // Drain cadence of the persistent kernel, in MMA steps of kMmaK reduction
-// elements: the main accumulator every `main` steps, the small one every
-// `small_every` main drains; periodic jobs write out every `write_every`
-// main drains.
+// elements: the accumulator every `main` steps; periodic jobs write out
+// every `write_every` drains.
 struct Cadence {
-  int main, small_every, write_every;
+  int main, write_every;
   int stall;  // test hook: the epilogue first waits on a barrier nothing arrives at
 };
 
@@ -231,10 +249,14 @@ constexpr int kStgCols = 8;
 constexpr int kStgPitch = kStgCols + 1;
 constexpr int kStgBytes = 32 * kStgPitch * 4;
 
-// Whole-tile staging (jobs with kTileStaging): the finished 128 x 128 FP32
-// tile, row pitch kTilePitch floats (no bank conflicts on column reads).
-constexpr int kTilePitch = kTileN + 1;
-constexpr int kTileStgBytes = kTileM * kTilePitch * 4;
+// Whole-tile staging (jobs with kTileStaging): the finished tile as its two
+// 16-bit slices, two planes of kPlaneElems elements each, laid out in the
+// order of the output runs (see PanelStagedJob).
+constexpr int kPlaneElems = 23040;
+constexpr int kTileStgBytes = 2 * kPlaneElems * 2;
+
+// Threads of a launch: producer, MMA issuer and the epilogue warps.
+constexpr int kThreads = (2 + kEpiWarps) * 32;
 
 template <int S, class Job>
 struct Smem {
@@ -247,10 +269,10 @@ struct Smem {
   static constexpr int kTotal = kOperandBytes + kStagingBytes + 256 + 1024;
 };
 
-// What a tile-staging job's epilogue needs besides its registers: the staging
-// area, two barriers over the epilogue warps (tile staged by every warp;
-// tile written out by every warp), the abort flag, the warp's index among
-// the epilogue warps and the number of tiles this CTA has written so far.
+// What a tile-staging job's epilogue needs besides its registers: the
+// staging area, two barriers (tile staged by every epilogue warp; staging
+// area free again), the abort flag, the warp's index among the epilogue
+// warps and the number of tiles this CTA has staged so far.
 struct EpiCtx {
   uint8_t* staging;
   uint64_t* staged;
@@ -628,10 +650,31 @@ struct PanelJob {
 //     tile starting at a pw boundary with (128 / n_ao) n_ao rows or the rest.
 //     For each (owner s, pw) the tile is the contiguous run
 //     Y[pw - Q0][seg(s) + aom n(s), + n(owner) n(s)].
-// The 16 epilogue warps stage the finished tile (true values, FP32) in shared
-// memory, then together write it out (mode 0 as 16-byte vectors) and add the
-// squared Frobenius norms of its atom blocks into norm2, one atomic per
-// rectangle (mu-atom x RI atom in mode 0, owner x pw in mode 1).
+// The 16 epilogue warps turn their accumulators into the two 16-bit slices
+// and store them in shared memory in the order of the output runs; on the
+// way they add the squared Frobenius norms of the tile's atom blocks into
+// norm2, one atomic per rectangle and group of rows (mu-atom x RI atom in
+// mode 0, owner x pw's RI atom in mode 1).  The runs then leave shared
+// memory:
+//   mode 0 (runs of 64 or 128 nsig elements): one epilogue warp issues one
+//     bulk copy per (run, slice) and returns to the accumulators; it waits
+//     for the copies' reads before the next tile is staged;
+//   mode 1 (runs of n(owner) n(s) elements, many per tile): the 16 warps copy
+//     the runs themselves, the 8-aligned body of each in 16-byte vectors and
+//     the few elements before and after it one by one.
+// A run starts in shared memory at the same offset modulo 8 elements as in
+// global memory, so that its body moves in aligned vectors:
+//   mode 0: run g at g (128 nsig + kRunSkew) (every X run is 8-aligned);
+//   mode 1: sigma-atom a of the tile owns a region at U_a + d_a, d_a = the
+//     global offset of its runs modulo 8, U_a = sum over the tile's earlier
+//     atoms b of round8(d_b + ng round8(n(owner) n(b))); run (a, g) at
+//     U_a + d_a + g round8(n(owner) n(a)).
+// The host checks that a tile fits in kPlaneElems (mode 1) and that the row
+// stride and the slice offset of the output are multiples of 8 elements.
+constexpr int kRunSkew = 16;  // mode 0 run pitch 128 nsig + 16: conflict-free staging stores
+
+__host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
+
 struct PanelStagedJob {
   const int4* tiles;          // (task, A row offset, B row offset, rows_valid << 16 | cols_valid)
   int n_tiles;
@@ -656,6 +699,9 @@ struct PanelStagedJob {
   static constexpr bool kPeriodic = false;
   static constexpr bool kTileStaging = true;
   static constexpr int kDrainHalves = 1;
+  // arrivals that free the staging area: the issuing warp (mode 0) or every
+  // epilogue warp (mode 1)
+  __device__ int freed_count() const { return mode == 0 ? 1 : kEpiWarps; }
 
   struct Tile {
     int ya, yb, ksteps, task, ra, rb, rv, cv;
@@ -695,128 +741,267 @@ struct PanelStagedJob {
     h0 = take_slice(v, f);
     h1 = take_slice(v, f);
   }
-  // The tile is staged in the output's own order, so that every output run is
-  // a contiguous run of the staging buffer:
-  //   mode 0: [pw run g][mu column c][s'],  position g 128 nsig + c nsig + s'
-  //   mode 1: per owner s (first tile row r_s): [column c][sigma' of s],
-  //           position ng nm r_s + c n(s) + sigma'  (c = g nm + mu', so the
-  //           run of (s, pw g) starts at ng nm r_s + g nm n(s))
-  __device__ bool write_staged(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
-                               EpiCtx& ep) const {
-    float* stg = reinterpret_cast<float*>(ep.staging);
-    const PanelTaskTC& tk = tasks[T.task];
-    // the previous tile has been written out by every epilogue warp
-    if (ep.tile_no > 0 && !mbar_wait(ep.freed, static_cast<uint32_t>(ep.tile_no - 1) & 1u, ep.abort))
-      return false;
-    const int r = quad * 32 + lane;  // this thread's tile row
-    if (mode == 0) {
-      const int nsig = tk.nsig;
-      if (r < T.rv) {
-        const int g = r / nsig, sp = r - g * nsig;
-        float* base = stg + g * kTileN * nsig + sp + c0 * nsig;
+  // Mode 1: global offset (row pw run 0) of the runs of sigma-atom a (task
+  // with RI base p0 and chunk-local owner AO offset aom).
+  __device__ long long run_dst(int p0, int aom, int pw0, int a) const {
+    return static_cast<long long>(p0 + pw0 - P0b) * ldk + rowbase[ao_off[a] - row_ao0] +
+           static_cast<long long>(aom) * n_ao[a];
+  }
+  // Mode 1: shared-memory extent of sigma-atom a's region (ng runs).
+  __device__ int region_len(int p0, int aom, int pw0, int ng, int nm, int a) const {
+    const int d = static_cast<int>(run_dst(p0, aom, pw0, a) & 7);
+    return round8(d + ng * round8(nm * n_ao[a]));
+  }
+
+  // Adds ss of every lane into the rectangle (row group key rk, column key
+  // ck >= 0); lanes with equal rk are contiguous.  uni: every row key of the
+  // warp is rk of lane 0 or -1.  Called by all 32 lanes.
+  __device__ __forceinline__ void add_norm(float ss, int rk, int ck, bool uni, int lane, int s_local,
+                                           int owner) const {
+    auto index = [&](int r) {
+      return mode == 0 ? (s_local * nmc + (ck - m_base)) * npa + (r - pa0)
+                       : ((r - s0b) * nmc + (owner - m_base)) * npa + (ck - pa0);
+    };
+    if (uni) {
 #pragma unroll
-        for (int j = 0; j < kEpiCols; ++j) base[j * nsig] = acc[j] * unscale;
-      }
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const int r0 = __shfl_sync(0xffffffffu, rk, 0);
+      if (lane == 0 && r0 >= 0 && ss != 0.f) atomicAdd(norm2 + index(r0), ss);
     } else {
-      const int nm = n_ao[tk.owner];
-      const int ng = T.cv / nm;
-      if (r < T.rv) {
+      flush_norm(ss, rk >= 0 ? index(rk) : -1, norm2, lane);
+    }
+  }
+
+  // Mode 1: run geometry of sigma-atom a in a tile of ng runs starting at pw
+  // run pw0: global offset of run 0 (d0), padded run pitch in shared memory
+  // (preg), head / 8-element vectors / tail of a run (h, nb, t) and the
+  // region length in shared memory (reg).
+  struct Geom {
+    long long d0;
+    int preg, h, nb, t, reg;
+  };
+  __device__ Geom geom(int p0, int aom, int pw0, int ng, int nm, int a) const {
+    Geom G;
+    const int len = nm * n_ao[a];
+    G.preg = round8(len);
+    G.d0 = run_dst(p0, aom, pw0, a);
+    const int d = static_cast<int>(G.d0 & 7);
+    G.h = min((8 - d) & 7, len);
+    G.nb = (len - G.h) >> 3;
+    G.t = len - G.h - 8 * G.nb;
+    G.reg = round8(d + ng * G.preg);
+    return G;
+  }
+
+  // Epilogue warps, end of a tile: wait until the staging area is free,
+  // stage this warp's 32 rows x 32 columns as slices, add the block norms,
+  // and copy the tile out (see above).
+  __device__ bool stage(float (&acc)[kEpiCols], const Tile& T, int quad, int lane, int c0,
+                        EpiCtx& ep) const {
+    uint16_t* pl0 = reinterpret_cast<uint16_t*>(ep.staging);
+    uint16_t* pl1 = pl0 + kPlaneElems;
+    uint16_t* o1 = out + slice_elems;
+    // the task's fields in registers before the first store or atomic (which
+    // the compiler cannot prove not to alias them)
+    const PanelTaskTC& tk = tasks[T.task];
+    const int t_nsig = tk.nsig, t_p0 = tk.p0, t_sl = tk.s_local, t_owner = tk.owner, t_aom = tk.aom;
+    const long long t_seg = tk.seg;
+    const bool f = f16 != 0;
+    const int r = quad * 32 + lane;  // this thread's tile row
+    const bool valid = r < T.rv;
+    int rk = -1;       // row group key: RI atom (mode 0) or sigma-atom (mode 1)
+    int ckl = -1;      // column key of column c0 + lane: mu-atom (mode 0) or RI atom (mode 1)
+    int pos = 0;       // staging position of column c0
+    int step = 0;      // mode 0: position step per column
+    int nm = 0, mu = 0, nsg = 0, gap = 0;  // mode 1 walk over (pw run, mu')
+    int ncol;          // columns that exist in the output
+    int sf = 0, sl = -1, ng = 0, pw0 = 0;
+    Geom G{0, 0, 0, 0, 0, 0};  // mode 1: lane i holds atom sf + i (first 32 atoms)
+    int g_U = 0;               // ... and its region's start
+    if (mode == 0) {
+      const int nsig = t_nsig;
+      const int gr = r / nsig, sp = r - gr * nsig;
+      pw0 = T.ra / nsig;
+      ng = T.rv / nsig;
+      ncol = min(kTileN, Lc - T.rb);
+      if (valid) rk = atom_of_ri[t_p0 + pw0 + gr];
+      if (c0 + lane < T.cv) ckl = atom_of_ao[mu_base + T.rb + c0 + lane];
+      step = nsig;
+      pos = gr * (kTileN * nsig + kRunSkew) + c0 * nsig + sp;
+    } else {
+      nm = t_nsig;  // the owner's function count
+      ng = T.cv / nm;
+      pw0 = T.rb / nm;
+      ncol = T.cv;
+      sf = atom_of_ao[row_ao0 + T.ra];
+      sl = atom_of_ao[row_ao0 + T.ra + T.rv - 1];
+      int s = sf, sp = 0;
+      if (valid) {
         const int a = row_ao0 + T.ra + r;
-        const int s = atom_of_ao[a];
-        const int nsg = n_ao[s], sp = a - ao_off[s];
-        float* base = stg + ng * nm * (r - sp) + sp + c0 * nsg;
+        s = atom_of_ao[a];
+        sp = a - ao_off[s];
+        nsg = n_ao[s];
+        rk = s;
+      }
+      if (sf + lane <= sl) G = geom(t_p0, t_aom, pw0, ng, nm, sf + lane);
+      int inc = sf + lane <= sl ? G.reg : 0;
+      const int mine = inc;
 #pragma unroll
-        for (int j = 0; j < kEpiCols; ++j)
-          if (c0 + j < T.cv) base[j * nsg] = acc[j] * unscale;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      g_U = inc - mine;
+      // U_s of this row's atom: from its lane, or summed when the tile has
+      // more than 32 atoms and s is past the first 32
+      int U = __shfl_sync(0xffffffffu, g_U, valid && s - sf <= 31 ? s - sf : 0);
+      if (valid && s - sf > 31) {
+        U = 0;
+        for (int b = sf; b < s; ++b) U += geom(t_p0, t_aom, pw0, ng, nm, b).reg;
+      }
+      if (valid) {
+        const int d = static_cast<int>(run_dst(t_p0, t_aom, pw0, s) & 7);
+        const int preg = round8(nm * nsg);
+        gap = preg - nm * nsg;
+        const int g = c0 / nm;
+        mu = c0 - g * nm;
+        pos = U + d + g * preg + mu * nsg + sp;
+      }
+      if (c0 + lane < T.cv) ckl = atom_of_ri[t_p0 + pw0 + (c0 + lane) / nm];
+    }
+    // the staging area is free: mode 0, the issuing warp's copies of the
+    // previous tile have read it; mode 1, every warp has copied its runs
+    if (ep.tile_no > 0) {
+      if (mode == 0 && ep.warp == 0) {
+        bulk_wait_read();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ep.freed);
+      }
+      if (!mbar_wait(ep.freed, static_cast<uint32_t>(ep.tile_no - 1) & 1u, ep.abort)) return false;
+    }
+    // row keys uniform across the warp's valid rows?
+    const int rk0 = __shfl_sync(0xffffffffu, rk, 0);
+    const bool uni = __all_sync(0xffffffffu, rk == rk0 || rk < 0);
+    // bit j: column j starts a new column key (warp-uniform)
+    const int ck_up = __shfl_up_sync(0xffffffffu, ckl, 1);
+    const unsigned kmask = __ballot_sync(0xffffffffu, lane == 0 || ckl != ck_up);
+    float ss = 0.f;
+#pragma unroll
+    for (int j = 0; j < kEpiCols; ++j) {
+      const float v = acc[j] * unscale;
+      if (valid && c0 + j < ncol) {
+        uint16_t h0, h1;
+        pack_slices(v * out_scale, f, h0, h1);
+        pl0[pos] = h0;
+        pl1[pos] = h1;
+        ss += v * v;
+      }
+      if (mode == 0) {
+        pos += step;
+      } else {
+        pos += nsg;
+        if (++mu == nm) {  // next pw run of the owner: the next padded slot
+          mu = 0;
+          pos += gap;
+        }
+      }
+      // the column key changes after column j: flush the segment
+      if (j == kEpiCols - 1 || ((kmask >> (j + 1)) & 1u)) {
+        const int ck = __shfl_sync(0xffffffffu, ckl, j);
+        if (ck >= 0) add_norm(ss, rk, ck, uni, lane, t_sl, t_owner);
+        ss = 0.f;
       }
     }
+    if (mode == 0) {
+      // the bulk copies read the staged slices through the async proxy
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ep.staged);
+      if (ep.warp != 0) return true;
+      if (!mbar_wait(ep.staged, static_cast<uint32_t>(ep.tile_no) & 1u, ep.abort)) return false;
+      const int nsig = t_nsig;
+      const int pitch = kTileN * nsig + kRunSkew;
+      const long long d0 = static_cast<long long>(t_p0 + pw0 - P0b) * ldk + t_seg +
+                           static_cast<long long>(T.rb) * nsig;
+      // X runs are 8-aligned by construction (segments of multiples of 64
+      // columns); refuse rather than issue a misaligned copy
+      if (((d0 | ldk | slice_elems) & 7) != 0 || ((ncol * nsig) & 7) != 0) return false;
+      const uint32_t bytes = static_cast<uint32_t>(ncol * nsig) * 2u;
+      bool issued = false;
+      for (int u = lane; u < 2 * ng; u += 32) {  // (run, slice) pairs
+        const int gr = u >> 1;
+        const long long dst = d0 + gr * ldk;
+        if (u & 1)
+          bulk_store(o1 + dst, pl1 + gr * pitch, bytes);
+        else
+          bulk_store(out + dst, pl0 + gr * pitch, bytes);
+        issued = true;
+      }
+      if (issued) bulk_commit();
+      return true;
+    }
+    // mode 1: every warp copies runs (atom i of the group, run g), warps
+    // striding over them
     __syncwarp();
     if (lane == 0) mbar_arrive(ep.staged);
     if (!mbar_wait(ep.staged, static_cast<uint32_t>(ep.tile_no) & 1u, ep.abort)) return false;
-    const bool f = f16 != 0;
-    const int tid = ep.warp * 32 + lane;
-    constexpr int kThr = kEpiWarps * 32;
-    if (mode == 0) {
-      const int nsig = tk.nsig;
-      const int ng = T.rv / nsig;               // pw runs in the tile
-      const int pw0 = T.ra / nsig;
-      const int mu0 = T.rb;                     // chunk-local
-      const int ncol = min(kTileN, Lc - mu0);   // X columns written (exact zeros past cv)
-      const int units = ncol * nsig / 8;        // 8-element vectors per run
-      for (int g = 0; g < ng; ++g) {
-        const float* run = stg + g * kTileN * nsig;
-        uint16_t* o0 = out + static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk + tk.seg +
-                       static_cast<long long>(mu0) * nsig;
-        for (int u = tid; u < units; u += kThr) {
-          const float4 va = *reinterpret_cast<const float4*>(run + 8 * u);
-          const float4 vb = *reinterpret_cast<const float4*>(run + 8 * u + 4);
-          const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-          uint32_t w0[4], w1[4];
+    int U0 = 0;  // first region of the current group of 32 atoms
+    for (int base = sf; base <= sl; base += 32) {
+      if (base > sf) {
+        G = Geom{0, 0, 0, 0, 0, 0};
+        if (base + lane <= sl) G = geom(t_p0, t_aom, pw0, ng, nm, base + lane);
+        int inc = base + lane <= sl ? G.reg : 0;
+        const int mine = inc;
 #pragma unroll
-          for (int k = 0; k < 8; k += 2) {
-            uint16_t a0, a1, b0, b1;
-            pack_slices(v[k] * out_scale, f, a0, a1);
-            pack_slices(v[k + 1] * out_scale, f, b0, b1);
-            w0[k / 2] = static_cast<uint32_t>(a0) | (static_cast<uint32_t>(b0) << 16);
-            w1[k / 2] = static_cast<uint32_t>(a1) | (static_cast<uint32_t>(b1) << 16);
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        g_U = inc - mine;
+      }
+      const int cnt = min(32, sl - base + 1);
+      for (int k = ep.warp; k < cnt * ng; k += kEpiWarps) {
+        const int i = k / ng, g = k - i * ng;
+        const long long d0 = __shfl_sync(0xffffffffu, G.d0, i);
+        const int preg = __shfl_sync(0xffffffffu, G.preg, i);
+        const int h = __shfl_sync(0xffffffffu, G.h, i);
+        const int nb = __shfl_sync(0xffffffffu, G.nb, i);
+        const int t = __shfl_sync(0xffffffffu, G.t, i);
+        const int R = U0 + __shfl_sync(0xffffffffu, g_U, i) + static_cast<int>(d0 & 7);
+        const long long dst = d0 + g * ldk;
+        const int src = R + g * preg;
+        // lane l: head element l < h, vector l - h < nb, tail element after
+        for (int l = lane; l < h + nb + t; l += 32) {
+          if (l < h) {
+            out[dst + l] = pl0[src + l];
+            o1[dst + l] = pl1[src + l];
+          } else if (l < h + nb) {
+            const int e = h + 8 * (l - h);
+            const uint4 x = *reinterpret_cast<const uint4*>(pl0 + src + e);
+            const uint4 y = *reinterpret_cast<const uint4*>(pl1 + src + e);
+            *reinterpret_cast<uint4*>(out + dst + e) = x;
+            *reinterpret_cast<uint4*>(o1 + dst + e) = y;
+          } else {
+            const int e = h + 8 * nb + (l - h - nb);
+            out[dst + e] = pl0[src + e];
+            o1[dst + e] = pl1[src + e];
           }
-          *reinterpret_cast<uint4*>(o0 + 8 * u) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-          *reinterpret_cast<uint4*>(o0 + slice_elems + 8 * u) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
         }
       }
-      // norms: rectangles (RI atom of the pw runs) x (mu-atom of the columns);
-      // a rectangle is, in each of its runs, one contiguous segment
-      const int pf = atom_of_ri[tk.p0 + pw0], pl = atom_of_ri[tk.p0 + pw0 + ng - 1];
-      const int mf = atom_of_ao[mu_base + mu0], ml = atom_of_ao[mu_base + mu0 + T.cv - 1];
-      const int np = pl - pf + 1;
-      for (int k = ep.warp; k < (ml - mf + 1) * np; k += kEpiWarps) {
-        const int m = mf + k / np, pa = pf + k % np;
-        const int g0 = max(0, ri_off[pa] - tk.p0 - pw0), g1 = min(ng, ri_off[pa + 1] - tk.p0 - pw0);
-        const int cc0 = max(0, ao_off[m] - mu_base - mu0), cc1 = min(T.cv, ao_off[m + 1] - mu_base - mu0);
-        float ss = 0.f;
-        for (int g = g0; g < g1; ++g) {
-          const float* seg = stg + g * kTileN * nsig + cc0 * nsig;
-          for (int i = lane; i < (cc1 - cc0) * nsig; i += 32) ss += seg[i] * seg[i];
-        }
+      // the group's total region length
+      int tot = base + lane <= sl ? G.reg : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0 && ss != 0.f)
-          atomicAdd(norm2 + (tk.s_local * nmc + (m - m_base)) * npa + (pa - pa0), ss);
-      }
-    } else {
-      const int nm = n_ao[tk.owner];            // mu' per pw run
-      const int ng = T.cv / nm;
-      const int pw0 = T.rb / nm;
-      const int sf = atom_of_ao[row_ao0 + T.ra], sl = atom_of_ao[row_ao0 + T.ra + T.rv - 1];
-      const int ns = sl - sf + 1;
-      // one region (owner s, pw run g) per warp in turn: write and norm together
-      for (int k = ep.warp; k < ns * ng; k += kEpiWarps) {
-        const int s = sf + k / ng, g = k % ng;
-        const int nsg = n_ao[s];
-        const int rs = ao_off[s] - row_ao0 - T.ra;   // tile row of sigma' = 0
-        const float* run = stg + ng * nm * rs + g * nm * nsg;
-        const long long dst = static_cast<long long>(tk.p0 + pw0 + g - P0b) * ldk +
-                              rowbase[ao_off[s] - row_ao0] + static_cast<long long>(tk.aom) * nsg;
-        const int len = nm * nsg;
-        float ss = 0.f;
-        for (int e = lane; e < len; e += 32) {
-          const float v = run[e];
-          ss += v * v;
-          uint16_t h0, h1;
-          pack_slices(v * out_scale, f, h0, h1);
-          out[dst + e] = h0;
-          out[slice_elems + dst + e] = h1;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        const int pa = atom_of_ri[tk.p0 + pw0 + g];
-        if (lane == 0 && ss != 0.f)
-          atomicAdd(norm2 + ((s - s0b) * nmc + (tk.owner - m_base)) * npa + (pa - pa0), ss);
-      }
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      U0 += tot;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(ep.freed);
     return true;
+  }
+
+  // After the last tile: the issuing warp's bulk copies have completed.
+  __device__ void finish(const EpiCtx& ep) const {
+    if (mode == 0 && ep.warp == 0) bulk_wait_all();
   }
 };
 
@@ -839,11 +1024,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kOperandBytes + L::kStagingBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
-  uint64_t* main_full = bars + 2 * kStages;  // [kMainBufs] main accumulator buffers
-  uint64_t* main_empty = main_full + kMainBufs;
-  uint64_t* small_full = main_empty + kMainBufs;  // the small accumulator
-  uint64_t* small_empty = small_full + 1;
-  uint64_t* drain = small_empty + 1;
+  uint64_t* acc_full = bars + 2 * kStages;  // [kAccBufs] accumulator buffers
+  uint64_t* acc_empty = acc_full + kAccBufs;
+  uint64_t* drain = acc_empty + kAccBufs;
   uint64_t* never = drain + 1;  // arrived at by nothing (stall test hook)
   uint64_t* tile_staged = never + 1;  // tile-staging jobs: every epilogue warp staged its part
   uint64_t* tile_freed = tile_staged + 1;  // ... and finished writing the tile out
@@ -856,16 +1039,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < kMainBufs; ++b) {
-      mbar_init(&main_full[b], 1);
-      mbar_init(&main_empty[b], kEpiWarps);
+    for (int b = 0; b < kAccBufs; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
     }
-    mbar_init(small_full, 1);
-    mbar_init(small_empty, kEpiWarps);
     mbar_init(drain, 1);
     mbar_init(never, 1);
     mbar_init(tile_staged, kEpiWarps);
-    mbar_init(tile_freed, kEpiWarps);
+    int freed_arrivals = 1;
+    if constexpr (Job::kTileStaging) freed_arrivals = job.freed_count();
+    mbar_init(tile_freed, static_cast<uint32_t>(freed_arrivals));
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -924,22 +1107,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    // Main product (0, 0) into a main buffer drained every cad.main MMA
-    // steps; the other products into a small buffer drained every
-    // cad.small_every main drains (their terms are 2^-8 or less of the main
-    // ones, so their accumulation error matters that much less).
+    // Each drain interval (cad.main MMA steps, or the tile's rest) goes to
+    // the next accumulator buffer; within the part of an interval that lies
+    // in one K step, the small slice products come first, then the main
+    // product (0, 0).
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f32(kTileM, kTileN, F16);
+      // slice tiles are kTileBytes apart: descriptor start addresses
+      // advance by kTileBytes >> 4
+      constexpr uint64_t kStep = static_cast<uint64_t>(L::kTileBytes >> 4);
       int stage = 0;
       uint32_t phase = 0;
-      int chunk = 0, schunk = 0;
+      int chunk = 0;
       bool ok = true, issued_any = false;
       for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
         const long long nsub = n * kSub;
         long long js = 0;
-        int sub = 0, cin = 0;  // MMA steps into the chunk; chunks into the small chunk
+        int sub = 0;  // MMA steps into the drain interval
         for (long long i = 0; i < n && ok; ++i) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
@@ -948,48 +1134,44 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(operands + stage * L::kStageBytes);
           const uint64_t da = desc_sw128(st), db = desc_sw128(st + S * L::kTileBytes);
-#pragma unroll
-          for (int k = 0; k < kSub; ++k) {
-            const int mb = chunk % kMainBufs;
-            if (ok && sub == 0) {
-              ok = mbar_wait(&main_empty[mb], ((static_cast<uint32_t>(chunk / kMainBufs)) & 1u) ^ 1u,
+          int k = 0;
+          while (k < kSub) {
+            const int mb = chunk % kAccBufs;
+            if (sub == 0) {
+              ok = mbar_wait(&acc_empty[mb], ((static_cast<uint32_t>(chunk / kAccBufs)) & 1u) ^ 1u,
                              abort_flag);
-              if (ok && cin == 0)
-                ok = mbar_wait(small_empty, (static_cast<uint32_t>(schunk) & 1u) ^ 1u, abort_flag);
               tc_fence_after();
+              if (!ok) break;
             }
-            if (ok) {
-              const uint32_t d_main = tmem + static_cast<uint32_t>(mb * 128);
-              const uint32_t d_small = tmem + kSmallCol;
-              const uint64_t koff = static_cast<uint64_t>((k * kMmaK * 2) >> 4);
-              mma_bf16(d_main, da + koff, db + koff, idesc, sub == 0 ? 0u : 1u);
-              const bool fresh = (sub == 0 && cin == 0);
-              bool first_small = true;
+            // MMA steps [k, ke) of this K step belong to the current interval
+            const int ke = min(kSub, k + (cad.main - sub));
+            const uint32_t d = tmem + static_cast<uint32_t>(mb * 128);
+            uint32_t accf = sub == 0 ? 0u : 1u;
+            for (int kk = k; kk < ke; ++kk) {
+              const uint64_t koff = static_cast<uint64_t>((kk * kMmaK * 2) >> 4);
 #pragma unroll
               for (int a = 0; a < S; ++a) {
 #pragma unroll
                 for (int b = 0; b < S - a; ++b) {
                   if (a == 0 && b == 0) continue;
-                  // slice tiles are kTileBytes apart: descriptor start
-                  // addresses advance by kTileBytes >> 4
-                  constexpr uint64_t kStep = static_cast<uint64_t>(L::kTileBytes >> 4);
-                  mma_bf16(d_small, da + a * kStep + koff, db + b * kStep + koff, idesc,
-                           (fresh && first_small) ? 0u : 1u);
-                  first_small = false;
+                  mma_bf16(d, da + a * kStep + koff, db + b * kStep + koff, idesc, accf);
+                  accf = 1u;
                 }
               }
-              issued_any = true;
-              ++js;
-              if (++sub == cad.main || js == nsub) {
-                mma_commit(&main_full[mb]);
-                ++chunk;
-                sub = 0;
-                if (++cin == cad.small_every || js == nsub) {
-                  mma_commit(small_full);
-                  ++schunk;
-                  cin = 0;
-                }
-              }
+            }
+            for (int kk = k; kk < ke; ++kk) {
+              const uint64_t koff = static_cast<uint64_t>((kk * kMmaK * 2) >> 4);
+              mma_bf16(d, da + koff, db + koff, idesc, accf);
+              accf = 1u;
+            }
+            issued_any = true;
+            js += ke - k;
+            sub += ke - k;
+            k = ke;
+            if (sub == cad.main || js == nsub) {
+              mma_commit(&acc_full[mb]);
+              ++chunk;
+              sub = 0;
             }
           }
           if (!ok) break;
@@ -1017,7 +1199,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* stg = staging + (warp - 2) * kStgBytes;
     const uint32_t row_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0);
     float acc[kEpiCols];
-    int chunk = 0, schunk = 0;
+    int chunk = 0;
     EpiCtx ep{staging, tile_staged, tile_freed, abort_flag, warp - 2, 0};
     (void)ep;
     // test hook: a dependency that is never satisfied; the bounded wait
@@ -1029,10 +1211,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long nch = (n * kSub + cad.main - 1) / cad.main;
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.f;
-      int cin = 0;
       for (long long c = 0; c < nch; ++c, ++chunk) {
-        const int mb = chunk % kMainBufs;
-        if (!mbar_wait(&main_full[mb], static_cast<uint32_t>(chunk / kMainBufs) & 1u, abort_flag)) {
+        const int mb = chunk % kAccBufs;
+        if (!mbar_wait(&acc_full[mb], static_cast<uint32_t>(chunk / kAccBufs) & 1u, abort_flag)) {
           ok = false;
           break;
         }
@@ -1040,20 +1221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_add32<Job::kDrainHalves>(row_addr + static_cast<uint32_t>(mb * 128), acc);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&main_empty[mb]);
-        if (++cin == cad.small_every || c + 1 == nch) {
-          if (!mbar_wait(small_full, static_cast<uint32_t>(schunk) & 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          tmem_add32<Job::kDrainHalves>(row_addr + kSmallCol, acc);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(small_empty);
-          ++schunk;
-          cin = 0;
-        }
+        if (lane == 0) mbar_arrive(&acc_empty[mb]);
         if constexpr (Job::kPeriodic) {
           if ((c + 1) % cad.write_every == 0 && c + 1 < nch) {
             job.write(acc, T, quad, lane, c0, stg);
@@ -1065,7 +1233,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       if (nch > 0) {
         if constexpr (Job::kTileStaging) {
-          ok = job.write_staged(acc, T, quad, lane, c0, ep);
+          ok = job.stage(acc, T, quad, lane, c0, ep);
           ++ep.tile_no;
           if (!ok) break;
         } else {
@@ -1073,6 +1241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    // bulk copies still in flight complete before the CTA exits
+    if constexpr (Job::kTileStaging) job.finish(ep);
     if (!ok) {
       *abort_flag = 1;
       if (lane == 0) atomicOr(err_flag, 4);
@@ -1568,7 +1738,6 @@ int launch_persistent(int slices, int f16, const CUtensorMap& ma, const CUtensor
   cad.stall = g_stall_test;
   cad.main = flush_k / tc::kMmaK > 0 ? flush_k / tc::kMmaK : 1;
   const int fk = cad.main * tc::kMmaK;
-  cad.small_every = tc::kSmallK / fk > 0 ? tc::kSmallK / fk : 1;
   cad.write_every = tc::kWriteK / fk > 0 ? tc::kWriteK / fk : 1;
   if (f16) {
     if (slices == 2) return launch_persistent_t<2, Job, true>(ma, mb, job, cad, err_flag, st);
@@ -1672,6 +1841,14 @@ int launch_group_tc(int slices, int f16, const CUtensorMap& ma, const CUtensorMa
   return launch_persistent(slices, f16, ma, mb, job, flush_k, err_flag, st);
 }
 
+bool staged_fits_mode1(int nm, const int* n_sig, int count) {
+  if (nm <= 0 || nm > tc::kTileN) return false;
+  const int ng = tc::kTileN / nm;
+  long long need = 0;
+  for (int i = 0; i < count; ++i) need += tc::round8(7 + ng * tc::round8(nm * n_sig[i]));
+  return need <= tc::kPlaneElems;
+}
+
 int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtensorMap& mg,
                            const CUtensorMap& mp, const int4* tiles, int n_tiles,
                            const PanelTaskTC* tasks, int mode, void* out, long long slice_elems,
@@ -1683,6 +1860,8 @@ int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtens
   tc::PanelStagedJob job{tiles, n_tiles, tasks, mode, static_cast<uint16_t*>(out), slice_elems, ldk,
                          P0b, Lc, row_ao0, s0b, rowbase, norm2, atom_of_ri, atom_of_ao, ao_off, ri_off,
                          n_ao, npa, pa0, mu_base, m_base, nmc, f16, unscale, out_scale};
+  // the staged runs leave in aligned 8-element vectors in both slices
+  if (ldk % 8 != 0 || slice_elems % 8 != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return -5;
   // mode 0: the panel rows are the A operand
   if (mode == 0) return launch_persistent(2, f16, mp, mg, job, flush_k, err_flag, st);
   return launch_persistent(2, f16, mg, mp, job, flush_k, err_flag, st);

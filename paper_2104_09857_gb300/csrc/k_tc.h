@@ -119,6 +119,9 @@ int launch_group_tc(int slices, int f16, const CUtensorMap& ma, const CUtensorMa
 // of the chunk; mode 1 A = batch rows of whole owner atoms (<= 128), B =
 // panel rows from a pw boundary.  Lc: chunk segment length (mode 0);
 // row_ao0, s0b: first AO and first owner atom of the batch (mode 1).
+// Needs ldk and slice_elems to be multiples of 8 (returns -5 otherwise) and,
+// in mode 1, every tile's staged runs to fit: staged_fits_mode1() of each
+// (owner function count, row group) pair.
 int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtensorMap& mg,
                            const CUtensorMap& mp, const int4* tiles, int n_tiles,
                            const PanelTaskTC* tasks, int mode, void* out, long long slice_elems,
@@ -127,6 +130,10 @@ int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtens
                            const int* atom_of_ao, const int* ao_off, const int* ri_off,
                            const int* n_ao, int npa, int pa0, int mu_base, int m_base, int nmc,
                            int flush_k, int* err_flag, cudaStream_t st);
+// Whether a mode-1 staged tile fits in the staging area: the owner has nm
+// functions and the tile's rows are the whole sigma-atoms with function
+// counts n_sig[0..count) (padding of every run taken at its worst).
+bool staged_fits_mode1(int nm, const int* n_sig, int count);
 // Zero the part of the step-B operand Y that step B does not write: for each
 // Y row (RI function Q0 + ql, ql < qrow) and batch atom s, the chunk-local mu
 // (chunk atoms [m0, m1), segment Lc functions) outside the owner atoms

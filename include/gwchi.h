@@ -408,7 +408,7 @@ int gw_evgw(gw_ctx* ctx, const double* V, int n_omega, const double* omega, cons
 /* Schedule search of the tensor-core chi route (no counterpart in the paper;
  * a tuner for this library's own schedule).  Searches, by coordinate descent
  * from the context's current options, the knobs that change only the order
- * and grouping of the work -- "panel_staged", "c_split_k", "batch_bytes"
+ * and grouping of the work -- "panel_staged", "c_split_k", "c_dynamic", "batch_bytes"
  * (0.5x, 1x, 1.5x of the current budget, where device memory allows) and
  * "mu_chunk_atoms" (automatic, n_atoms/4, n_atoms/2) -- timing each candidate
  * as the device time of gw_chi_tau on tau point tau_index (one untimed call
@@ -471,6 +471,10 @@ int gw_get_stats(const gw_ctx* ctx, gw_stats* out);
  *                  chi with FP64 atomics, so the summation order (and the
  *                  last bits) vary from run to run; 0 = one unit per tile,
  *                  bitwise reproducible (default 2048)
+ *   "c_dynamic"    split forms with c_split_k > 0: 1 (default) the CTAs take
+ *                  the step-C units in order from a shared counter, so that
+ *                  the units in flight read few operand slabs; 0 each CTA
+ *                  takes a fixed share (every 152nd unit)
  *   "c_order"      with c_split_k = 0: tile order, 0 longest first (default),
  *                  1 grouped raster
  *   "mlp_margin"   learned screening: decades added to the predicted norm

@@ -1442,10 +1442,12 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     ctx->stats.kernel_launches += 5;
     ctx->tc_issue_per_k = 2.0 * tile * tile * prods;
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
+    int* d_work;  // the units' counter (zeroed by the launch)
+    if ((rc = wsT(ctx, "tc_work", 1, &d_work))) return rc;
     if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, w.u_tile, w.u_first,
                                 w.u_count, (int)std::min<size_t>(cap, INT32_MAX), w.n_units, tasks,
                                 counts, nslab, d_k0, d_len, b.P0, prow, nri, b.Q0, qrow, nqt, acc,
-                                ctx->flush_k, d_err, ctx->stream))
+                                ctx->flush_k, ctx->c_dynamic ? d_work : nullptr, d_err, ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
     GW_CHECK_LAUNCH();
     GW_TRY(cudaEventRecord(ec1, ctx->stream));
@@ -1536,11 +1538,13 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
     if ((rc = upload(ctx, "unit_tile", u_tile, &d_ut))) return rc;
     if ((rc = upload(ctx, "unit_first", u_first, &d_uf))) return rc;
     if ((rc = upload(ctx, "unit_count", u_count, &d_uc))) return rc;
+    int* d_work;  // the units' counter (zeroed by the launch)
+    if ((rc = wsT(ctx, "tc_work", 1, &d_work))) return rc;
     GW_TRY(cudaEventRecord(ec0, ctx->stream));
     if (gw::launch_chi_tc_units(slices, f16, (float)(1.0 / (s_x * s_y)), mx, my, d_ut, d_uf, d_uc,
                                 (int)u_tile.size(), nullptr, tasks, counts,
                                 nslab, d_k0, d_len, b.P0, prow, nri, b.Q0, qrow, nqt, acc, ctx->flush_k,
-                                d_err, ctx->stream))
+                                ctx->c_dynamic ? d_work : nullptr, d_err, ctx->stream))
       return fail(ctx, GW_ERR_CUDA, "tensor-core step C launch setup failed");
   } else {
     int* d_active;
@@ -1906,6 +1910,11 @@ int gw_set_option(gw_ctx* ctx, const char* key, double value) {
   }
   if (!strcmp(key, "test_stall_tc")) {
     ctx->test_stall = value != 0.0;
+    return GW_OK;
+  }
+  if (!strcmp(key, "c_dynamic")) {
+    if (value != 0 && value != 1) return fail(ctx, GW_ERR_INVALID_ARG, "c_dynamic must be 0 or 1");
+    ctx->c_dynamic = (int)value;
     return GW_OK;
   }
   if (!strcmp(key, "c_split_k")) {

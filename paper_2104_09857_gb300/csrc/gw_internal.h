@@ -252,6 +252,9 @@ struct gw_ctx {
   // step-C work units: tiles split into runs of about c_split_k reduction
   // elements, FP64 atomics into chi (0: whole tiles, bitwise reproducible)
   int c_split_k = 2048;
+  // step-C work units handed out in order from a counter (1) or a fixed
+  // share per CTA (0)
+  int c_dynamic = 1;
   // mu-atoms per chunk of the tensor-core route's 2-D batches (0: the fewest
   // equal chunks that keep one owner's operands within budget / 8)
   int mu_chunk_atoms = 0;

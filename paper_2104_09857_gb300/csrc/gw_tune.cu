@@ -31,6 +31,7 @@ struct Knob {
 double current(const gw_ctx* ctx, const std::string& k) {
   if (k == "panel_staged") return ctx->panel_staged;
   if (k == "c_split_k") return ctx->c_split_k;
+  if (k == "c_dynamic") return ctx->c_dynamic;
   if (k == "batch_bytes") return ctx->batch_bytes;
   if (k == "mu_chunk_atoms") return ctx->mu_chunk_atoms;
   return 0.0;
@@ -79,6 +80,7 @@ extern "C" int gw_autotune(gw_ctx* ctx, int tau_index, double thr, int precision
   std::vector<Knob> knobs = {
       {"panel_staged", {1, 0}},
       {"c_split_k", {1024, 2048, 4096, 8192}},
+      {"c_dynamic", {1, 0}},
       {"batch_bytes", budgets},
       {"mu_chunk_atoms", {0, (double)std::max(1, ctx->n_at / 4), (double)std::max(1, ctx->n_at / 2)}},
   };

@@ -300,8 +300,10 @@ struct ChiJob {
   double* chi;      // chi + Q0 (row stride nri)
   float out_scale;  // 1 / (scale of the A operand x scale of the B operand)
   const int* n_dev; // optional: number of units in device memory (n_tiles = capacity)
+  int* work;        // optional: counter handing the units out in order (zeroed before the launch)
   static constexpr bool kPeriodic = true;
   static constexpr bool kTileStaging = false;
+  static constexpr bool kDynamic = true;
   static constexpr int kDrainHalves = 2;  // 96 registers: one 32-column load would spill
 
   struct Tile {
@@ -413,6 +415,7 @@ struct GroupJob {
   double* out;
   static constexpr bool kPeriodic = true;
   static constexpr bool kTileStaging = false;
+  static constexpr bool kDynamic = false;
   static constexpr int kDrainHalves = 2;
 
   struct Tile {
@@ -513,6 +516,7 @@ struct PanelJob {
   float out_scale;            // scale of the Z slices
   static constexpr bool kPeriodic = false;
   static constexpr bool kTileStaging = false;
+  static constexpr bool kDynamic = false;
   static constexpr int kDrainHalves = 1;
 
   struct Tile {
@@ -698,6 +702,7 @@ struct PanelStagedJob {
   float unscale, out_scale;
   static constexpr bool kPeriodic = false;
   static constexpr bool kTileStaging = true;
+  static constexpr bool kDynamic = false;
   static constexpr int kDrainHalves = 1;
   // arrivals that free the staging area: the issuing warp (mode 0) or every
   // epilogue warp (mode 1)
@@ -1006,6 +1011,85 @@ struct PanelStagedJob {
 };
 
 // ---------------------------------------------------------------------------
+// work distribution
+// ---------------------------------------------------------------------------
+constexpr int kSchedSlots = 4;
+// The work items of one role of a CTA: blockIdx.x, + gridDim.x, ... (static),
+// or, for a job that hands items out from an atomic counter, whatever item
+// the producer thread takes next: it passes each to the MMA issuer and the
+// epilogue warps through a ring of shared-memory slots, so that the CTAs
+// together work through the items in order (and the operand slabs of the
+// items in flight stay few).  -1 ends the sequence.
+struct Sched {
+  volatile int* slot;  // [kSchedSlots]
+  uint64_t* full;      // [kSchedSlots] item written by the producer
+  uint64_t* empty;     // [kSchedSlots] item read by the MMA issuer and every epilogue warp
+  int* counter;        // null: static
+  int n;
+  volatile int* abort;
+  int s;
+  uint32_t ph;
+  int t;               // static: the next item
+  __device__ int next_static() {
+    const int v = t;
+    t += gridDim.x;
+    return v < n ? v : -1;
+  }
+  __device__ void advance() {
+    if (++s == kSchedSlots) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+  // producer (one thread)
+  __device__ int produce(bool& ok) {
+    if (!counter) return next_static();
+    if (!mbar_wait(&empty[s], ph ^ 1u, abort)) {
+      ok = false;
+      return -1;
+    }
+    int v = atomicAdd(counter, 1);
+    if (v >= n) v = -1;
+    slot[s] = v;
+    mbar_arrive(&full[s]);
+    advance();
+    return v;
+  }
+  // the MMA issuer (one thread)
+  __device__ int consume_one(bool& ok) {
+    if (!counter) return next_static();
+    if (!mbar_wait(&full[s], ph, abort)) {
+      ok = false;
+      return -1;
+    }
+    const int v = slot[s];
+    mbar_arrive(&empty[s]);
+    advance();
+    return v;
+  }
+  // an epilogue warp (all 32 lanes)
+  __device__ int consume_warp(int lane, bool& ok) {
+    if (!counter) return next_static();
+    if (!mbar_wait(&full[s], ph, abort)) {
+      ok = false;
+      return -1;
+    }
+    const int v = slot[s];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    advance();
+    return v;
+  }
+};
+template <class Job>
+__device__ int* work_counter(const Job& j) {
+  if constexpr (Job::kDynamic)
+    return j.work;
+  else
+    return nullptr;
+}
+
+// ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 template <int S, class Job, bool F16>
@@ -1030,7 +1114,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* never = drain + 1;  // arrived at by nothing (stall test hook)
   uint64_t* tile_staged = never + 1;  // tile-staging jobs: every epilogue warp staged its part
   uint64_t* tile_freed = tile_staged + 1;  // ... and finished writing the tile out
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_freed + 1);
+  uint64_t* sched_full = tile_freed + 1;           // [kSchedSlots]
+  uint64_t* sched_empty = sched_full + kSchedSlots;  // [kSchedSlots]
+  int* sched_slot = reinterpret_cast<int*>(sched_empty + kSchedSlots);  // [kSchedSlots]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sched_slot + kSchedSlots);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
 
@@ -1049,6 +1136,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     int freed_arrivals = 1;
     if constexpr (Job::kTileStaging) freed_arrivals = job.freed_count();
     mbar_init(tile_freed, static_cast<uint32_t>(freed_arrivals));
+    for (int k = 0; k < kSchedSlots; ++k) {
+      mbar_init(&sched_full[k], 1);
+      mbar_init(&sched_empty[k], 1 + kEpiWarps);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1063,6 +1154,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int n_items = job.items();  // work items (tiles or units) of the launch
+  Sched sch{sched_slot, sched_full, sched_empty, work_counter(job), n_items, abort_flag, 0, 0,
+            static_cast<int>(blockIdx.x)};
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -1073,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool armed[kStages];
       for (int s = 0; s < kStages; ++s) armed[s] = false, armed_parity[s] = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+      for (int t = sch.produce(ok); t >= 0 && ok; t = sch.produce(ok)) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
         typename Job::Iter it;
@@ -1120,7 +1213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int chunk = 0;
       bool ok = true, issued_any = false;
-      for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+      for (int t = sch.consume_one(ok); t >= 0 && ok; t = sch.consume_one(ok)) {
         const typename Job::Tile T = job.tile(t);
         const long long n = job.nsteps(T);
         const long long nsub = n * kSub;
@@ -1205,7 +1298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // test hook: a dependency that is never satisfied; the bounded wait
     // gives up and the kernel reports a time-out instead of hanging
     bool ok = cad.stall ? mbar_wait(never, 0, abort_flag) : true;
-    for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+    for (int t = ok ? sch.consume_warp(lane, ok) : -1; t >= 0 && ok; t = sch.consume_warp(lane, ok)) {
       const typename Job::Tile T = job.tile(t);
       const long long n = job.nsteps(T);
       const long long nch = (n * kSub + cad.main - 1) / cad.main;
@@ -1777,7 +1870,7 @@ int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, c
                   int qrow, int nqt, double* chi, int flush_k, int* err_flag, cudaStream_t st) {
   (void)qrow;
   tc::ChiJob job{tile_list, n_tiles, nullptr, nullptr, tasks, counts, max_slab, slab_k0, slab_len, nqt,
-                 P0, prow, nri, nri - Q0, chi + Q0, out_scale, nullptr};
+                 P0, prow, nri, nri - Q0, chi + Q0, out_scale, nullptr, nullptr};
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 
@@ -1786,10 +1879,11 @@ int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap&
                         const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
                         const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
                         int P0, int prow, int nri, int Q0, int qrow, int nqt, double* chi, int flush_k,
-                        int* err_flag, cudaStream_t st) {
+                        int* work, int* err_flag, cudaStream_t st) {
   (void)qrow;
   tc::ChiJob job{unit_tile, n_units, unit_first, unit_count, tasks, counts, max_slab, slab_k0, slab_len,
-                 nqt, P0, prow, nri, nri - Q0, chi + Q0, out_scale, n_units_dev};
+                 nqt, P0, prow, nri, nri - Q0, chi + Q0, out_scale, n_units_dev, work};
+  if (work && cudaMemsetAsync(work, 0, sizeof(int), st) != cudaSuccess) return -6;
   return launch_persistent(slices, f16, mx, my, job, flush_k, err_flag, st);
 }
 

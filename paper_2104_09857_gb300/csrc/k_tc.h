@@ -45,13 +45,15 @@ int launch_chi_tc(int slices, int f16, float out_scale, const CUtensorMap& mx, c
 // unit_tile[u] over list entries [unit_first[u], unit_first[u] + unit_count[u])
 // of that tile's task list and adds into chi with FP64 atomics.  The number
 // of units is n_units, or *n_units_dev (device memory) when that is not null,
-// n_units then being the capacity of the unit arrays.
+// n_units then being the capacity of the unit arrays.  work (one device int,
+// zeroed here on the stream; may be null): the CTAs take the units in order
+// from this counter instead of a fixed share each.
 int launch_chi_tc_units(int slices, int f16, float out_scale, const CUtensorMap& mx,
                         const CUtensorMap& my, const int* unit_tile, const int* unit_first,
                         const int* unit_count, int n_units, const int* n_units_dev, const int* tasks,
                         const int* counts, int max_slab, const long long* slab_k0, const int* slab_len,
                         int P0, int prow, int nri, int Q0, int qrow, int nqt, double* chi, int flush_k,
-                        int* err_flag, cudaStream_t st);
+                        int* work, int* err_flag, cudaStream_t st);
 // Device scratch of launch_plan_units: per tile (ntiles) ucnt, uoff; per unit
 // (capacity ntiles * nslab) t_tile, t_first, t_count, t_key, u_tile, u_first,
 // u_count; per slab (nslab) hist, start; and the counters n_units,

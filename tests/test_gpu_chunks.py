@@ -188,3 +188,17 @@ def test_streamed_panels_give_the_same_chi(lib, chunk, fp32):
     assert np.array_equal(a, b)
     assert sa["flops_useful"] == sb["flops_useful"]
     _check(a, oc.chi_dense(case), 1e-6)
+
+
+@pytest.mark.parametrize("dynamic", [0, 1])
+def test_step_c_unit_distribution(lib, dynamic):
+    """Step-C units taken in order from a shared counter (default) or as a
+    fixed share per CTA give the same chi within the bar, with the same
+    useful flops (only the order of the FP64 atomic adds differs)."""
+    case = make_case("ribbon28", n_tau=2)
+    ref = oc.chi_dense(case)
+    got, st = _run(lib, case, "fp16x3", case.thr, {"c_dynamic": dynamic, "c_split_k": 1024})
+    _check(got, ref, 1e-6)
+    got0, st0 = _run(lib, case, "fp16x3", case.thr, {"c_dynamic": 1 - dynamic, "c_split_k": 1024})
+    assert st["flops_c"] == st0["flops_c"]
+    assert np.allclose(got, got0, rtol=0, atol=1e-12 * np.abs(got0).max())

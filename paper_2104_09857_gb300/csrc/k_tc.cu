@@ -1449,13 +1449,16 @@ __global__ void k_slices_block_flags(const int* __restrict__ ri_off, int rowoff,
 }
 
 // Zero, in every slice, the blocks queued by k_slices_block_flags: one warp
-// per queued block, the warps striding over the queue.
+// per queued block, the warps striding over the queue.  Each row of a block
+// is one contiguous run: its 8-aligned body in 16-byte stores, the elements
+// before and after one by one (slice_elems and ldk are multiples of 8 when
+// vec is set).
 __global__ void k_slices_zero_blocks(uint16_t* __restrict__ Z, int slices, long long slice_elems,
                                      long long ldk, int rowoff, const int* __restrict__ ri_off,
                                      const int* __restrict__ ao_off, const int* __restrict__ n_ao,
                                      int s0, const long long* __restrict__ seg, int pa0, int npa,
                                      int m0, int nmc, int mu0, const int* __restrict__ zlist,
-                                     const int* __restrict__ zcount) {
+                                     const int* __restrict__ zcount, int vec) {
   const int lane = threadIdx.x & 31;
   const int nq = *zcount;
   const int nwarps = gridDim.x * (blockDim.x / 32);
@@ -1470,10 +1473,29 @@ __global__ void k_slices_zero_blocks(uint16_t* __restrict__ Z, int slices, long 
     const int rows0 = ri_off[p] - rowoff, nrows = ri_off[p + 1] - ri_off[p];
     const long long c0 = seg[sl] + static_cast<long long>(ao_off[m] - mu0) * nsig;
     const int ncols = n_ao[m] * nsig;
-    for (int r = 0; r < nrows; ++r)
-      for (int c = lane; c < ncols; c += 32)
-        for (int sc = 0; sc < slices; ++sc)
-          Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = 0;  // +0 in both formats
+    if (vec) {
+      for (int r = 0; r < nrows; ++r) {
+        const long long row = static_cast<long long>(rows0 + r) * ldk + c0;
+        const int h = min(static_cast<int>((8 - (row & 7)) & 7), ncols);
+        const int nb = (ncols - h) >> 3, t = ncols - h - 8 * nb;
+        for (int l = lane; l < h + nb + t; l += 32) {
+          for (int sc = 0; sc < slices; ++sc) {
+            uint16_t* z = Z + sc * slice_elems + row;
+            if (l < h)
+              z[l] = 0;  // +0 in both formats
+            else if (l < h + nb)
+              *reinterpret_cast<uint4*>(z + h + 8 * (l - h)) = make_uint4(0, 0, 0, 0);
+            else
+              z[h + 8 * nb + (l - h - nb)] = 0;
+          }
+        }
+      }
+    } else {
+      for (int r = 0; r < nrows; ++r)
+        for (int c = lane; c < ncols; c += 32)
+          for (int sc = 0; sc < slices; ++sc)
+            Z[sc * slice_elems + static_cast<long long>(rows0 + r) * ldk + c0 + c] = 0;
+    }
   }
 }
 
@@ -2019,9 +2041,10 @@ void launch_slices_block_filter(void* Z, int slices, long long slice_elems, long
       ri_off, rowoff, pa0, npa, nmc, ns, thr, norm2, blockflag, tileflag, ntile, tile_rows, zlist,
       zcount);
   // many warps: each queued block is a few kilobytes of scattered rows
+  const int vec = (slice_elems % 8 == 0 && ldk % 8 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0) ? 1 : 0;
   tc::k_slices_zero_blocks<<<152 * 64, 256, 0, st>>>(static_cast<uint16_t*>(Z), slices, slice_elems, ldk,
                                                   rowoff, ri_off, ao_off, n_ao, s0, seg, pa0, npa, m0,
-                                                  nmc, mu0, zlist, zcount);
+                                                  nmc, mu0, zlist, zcount, vec);
 }
 
 }  // namespace gw

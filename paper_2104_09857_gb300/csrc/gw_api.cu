@@ -1158,11 +1158,31 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
   // ---- step A: X[P][(s, mu, s')] for the owners of the batch, rows mu of the chunk ----
   {
     const int rows_a = (b.nmu + tile - 1) / tile * tile;
+    const int nmt = rows_a / tile;
     std::vector<gw::PanelTaskTC> ta;
     std::vector<int4> tiles;
+    // mu tiles of the chunk whose G^occ rows against every lambda atom of
+    // the owner's panel are dropped blocks (zero) give exact zeros: X is
+    // zeroed before the step, so they are left out.  Their X blocks keep
+    // zero norms, and step C never lists their slabs.
+    std::vector<char> live(nmt, 1), reach(n_at, 0);
     for (int s = b.s0; s < b.s1; ++s) {
       gw::PanelTaskTC t = ctx->pt_tasks[s];
       if (t.K == 0) continue;
+      if (ctx->cur_fo) {
+        const std::vector<unsigned char>& fo = *ctx->cur_fo;
+        std::fill(reach.begin(), reach.end(), 0);
+        for (int i = ctx->wl_off[s]; i < ctx->wl_off[s + 1]; ++i) {
+          const size_t a = (size_t)ctx->wl_atom[i] * n_at;
+          for (int m = b.m0; m < b.m1; ++m) reach[m] |= fo[a + m];
+        }
+        for (int mt = 0; mt < nmt; ++mt) {
+          const int c0 = b.mu0 + mt * tile, c1 = std::min(b.mu0 + b.nmu, c0 + tile) - 1;
+          char on = 0;
+          for (int m = ctx->h_atom_of_ao[c0]; m <= ctx->h_atom_of_ao[c1] && !on; ++m) on = reach[m];
+          live[mt] = on;
+        }
+      }
       if (ctx->pt_stream) t.p_row0 = row0A[s];
       t.g_row0 = (int)ta.size() * rows_a;
       t.seg = b.seg[s - b.s0];
@@ -1170,18 +1190,25 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (staged) {
         // panel rows from pw boundaries: (tile / nsig) whole runs per tile
         const int meff = tile / t.nsig * t.nsig;
-        int ntn = 0;
+        int ntn = 0, nlive = 0;
         for (int ra = 0; ra < t.N; ra += meff, ++ntn)
-          for (int mt = 0; mt < rows_a / tile; ++mt) {
+          for (int mt = 0; mt < nmt; ++mt) {
+            if (!live[mt]) continue;
             const int rv = std::min(meff, t.N - ra), cv = std::min(tile, b.nmu - mt * tile);
             tiles.push_back(make_int4((int)ta.size(), ra, mt * tile, (rv << 16) | cv));
+            ++nlive;
           }
-        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * nlive;
       } else {
         const int ntn = (t.N + tile - 1) / tile;
+        int nlive = 0;
         for (int nt = 0; nt < ntn; ++nt)
-          for (int mt = 0; mt < rows_a / tile; ++mt) tiles.push_back(make_int4((int)ta.size(), nt, mt, 0));
-        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * (rows_a / tile) * ntn;
+          for (int mt = 0; mt < nmt; ++mt)
+            if (live[mt]) {
+              tiles.push_back(make_int4((int)ta.size(), nt, mt, 0));
+              ++nlive;
+            }
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * nlive;
       }
       ta.push_back(t);
     }
@@ -1240,6 +1267,12 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
             staged_b = false;
             break;
           }
+    // staged: a (row group, owner) pair whose G^virt rows against every
+    // lambda atom of the owner's panel are dropped blocks gives exact zeros;
+    // its tiles are left out and its Y runs zeroed by a store-only kernel
+    // (Y is not zeroed as a whole before the step)
+    std::vector<gw::DeadY> dead;
+    std::vector<char> reachv(n_at, 0), glive(groups.size(), 1);
     for (int m = b.m0; m < b.m1; ++m) {
       gw::PanelTaskTC t = ctx->pt_tasks[m];
       if (t.K == 0) continue;
@@ -1247,14 +1280,33 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       t.aom -= b.mu0;  // chunk-local first AO of the panel's owner
       t.g_row0 = (int)tb.size() * rows_b;
       if (staged_b) {
+        if (ctx->cur_fv) {
+          const std::vector<unsigned char>& fv = *ctx->cur_fv;
+          std::fill(reachv.begin(), reachv.end(), 0);
+          for (int i = ctx->wl_off[m]; i < ctx->wl_off[m + 1]; ++i) {
+            const size_t a = (size_t)ctx->wl_atom[i] * n_at;
+            for (int s = b.s0; s < b.s1; ++s) reachv[s] |= fv[a + s];
+          }
+          for (size_t gi = 0; gi < groups.size(); ++gi) {
+            char on = 0;
+            for (int s = group_atoms[gi].first; s < group_atoms[gi].second && !on; ++s) on = reachv[s];
+            glive[gi] = on;
+            if (!on)
+              dead.push_back(gw::DeadY{t.p0 - b.Q0, t.npw, group_atoms[gi].first - b.s0,
+                                       group_atoms[gi].second - b.s0, t.aom, t.nsig});
+          }
+        }
         const int meff = tile / t.nsig * t.nsig;  // whole runs of the owner's functions
-        int ntn = 0;
-        for (int rb = 0; rb < t.N; rb += meff, ++ntn)
-          for (const auto& g : groups) {
+        int nlive = 0;
+        for (int rb = 0; rb < t.N; rb += meff)
+          for (size_t gi = 0; gi < groups.size(); ++gi) {
+            if (!glive[gi]) continue;
+            const auto& g = groups[gi];
             const int cv = std::min(meff, t.N - rb);
             tiles.push_back(make_int4((int)tb.size(), g.first, rb, (g.second << 16) | cv));
+            ++nlive;
           }
-        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * groups.size() * ntn;
+        issued += 2.0 * tile * tile * 64.0 * t.ksteps * prods * nlive;
       } else {
         const int ntn = (t.N + tile - 1) / tile;
         for (int nt = 0; nt < ntn; ++nt)
@@ -1304,6 +1356,16 @@ int chi_one_batch_tc(gw_ctx* ctx, const Batch& b, const double* g_occ, const dou
       if (lrc) return fail(ctx, GW_ERR_CUDA, "tensor-core step B launch setup failed");
       GW_CHECK_LAUNCH();
       ctx->stats.kernel_launches += 2;
+      if (!dead.empty()) {
+        gw::DeadY* d_dead;
+        long long* d_segb;
+        if ((rc = upload(ctx, "dead_y", dead, &d_dead))) return rc;
+        if ((rc = upload(ctx, "seg_b", b.seg, &d_segb))) return rc;
+        gw::launch_zero_dead_y(ys, slices, (long long)qrow * Kb, Kb, qrow, d_dead, (int)dead.size(), d_segb,
+                               d_nao_a, b.s0, ctx->stream);
+        GW_CHECK_LAUNCH();
+        ctx->stats.kernel_launches += 1;
+      }
     }
   }
   GW_TRY(cudaEventRecord(ea1, ctx->stream));
@@ -1741,6 +1803,7 @@ int gw_set_basis(gw_ctx* ctx, int n_atoms, const double* xyz, const int* n_ao, c
     for (int i = ctx->ri_off[a]; i < ctx->ri_off[a + 1]; ++i) atom_of_ri[i] = a;
     for (int i = ctx->ao_off[a]; i < ctx->ao_off[a + 1]; ++i) atom_of_ao[i] = a;
   }
+  ctx->h_atom_of_ao = atom_of_ao;
   free_dev(ctx->d_ao_off);
   free_dev(ctx->d_ri_off);
   free_dev(ctx->d_atom_of_ri);
@@ -2127,6 +2190,8 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
     double fa = 0.0, fb = 0.0;
     std::vector<double> kao;
     int kao_m0 = -1;
+    ctx->cur_fo = thr > 0.0 ? &hfo : nullptr;
+    ctx->cur_fv = thr > 0.0 ? &hfv : nullptr;
     for (size_t bi = 0; bi < batches.size(); ++bi) {
       const Batch& b = batches[bi];
       // useful flops of steps A and B; a batch whose X or Y is all zero
@@ -2149,8 +2214,12 @@ int gw_chi_tau(gw_ctx* ctx, int tau_first, int tau_count, double thr, int precis
         rc = chi_one_batch_tc(ctx, b, go, gv, thr, acc, fc, precision, bi);
       else
         rc = chi_one_batch<float>(ctx, b, go32, gv32, ctx->d_panel32, thr, acc, fc, precision, bi);
-      if (rc) return rc;
+      if (rc) {
+        ctx->cur_fo = ctx->cur_fv = nullptr;
+        return rc;
+      }
     }
+    ctx->cur_fo = ctx->cur_fv = nullptr;
     GW_TRY(cudaEventRecord(ev[2], ctx->stream));
     double* dst = out_on_device ? chi_out + (size_t)(j - tau_first) * nri * nri : stage;
     gw::launch_mirror(acc, dst, nri, ctx->d_atom_of_ri, ctx->stream);

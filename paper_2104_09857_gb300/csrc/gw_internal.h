@@ -142,6 +142,7 @@ struct gw_ctx {
   int* d_ri_off = nullptr;
   int* d_atom_of_ri = nullptr;
   int* d_atom_of_ao = nullptr;
+  std::vector<int> h_atom_of_ao;  // host copy
 
   // three-centre tensor (A <= B blocks as given)
   long long n_blocks = 0, n_elems = 0;
@@ -255,6 +256,11 @@ struct gw_ctx {
   // step-C work units handed out in order from a counter (1) or a fixed
   // share per CTA (0)
   int c_dynamic = 1;
+  // G block flags of the current tau point (host copies, n_at x n_at; null
+  // or all kept when nothing is filtered): steps A/B leave out the tiles
+  // whose G rows are all dropped blocks
+  const std::vector<unsigned char>* cur_fo = nullptr;
+  const std::vector<unsigned char>* cur_fv = nullptr;
   // mu-atoms per chunk of the tensor-core route's 2-D batches (0: the fewest
   // equal chunks that keep one owner's operands within budget / 8)
   int mu_chunk_atoms = 0;

@@ -1030,6 +1030,7 @@ struct Sched {
   int s;
   uint32_t ph;
   int t;               // static: the next item
+  int ahead;           // dynamic: the producer's next item, taken one item early (-2: none yet)
   __device__ int next_static() {
     const int v = t;
     t += gridDim.x;
@@ -1048,8 +1049,11 @@ struct Sched {
       ok = false;
       return -1;
     }
-    int v = atomicAdd(counter, 1);
+    // the counter's next value is fetched while this item runs; the counter
+    // only grows, so the value left unused after the last item is past n
+    int v = ahead >= -1 ? ahead : atomicAdd(counter, 1);
     if (v >= n) v = -1;
+    ahead = v >= 0 ? atomicAdd(counter, 1) : -1;
     slot[s] = v;
     mbar_arrive(&full[s]);
     advance();
@@ -1155,7 +1159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const int n_items = job.items();  // work items (tiles or units) of the launch
   Sched sch{sched_slot, sched_full, sched_empty, work_counter(job), n_items, abort_flag, 0, 0,
-            static_cast<int>(blockIdx.x)};
+            static_cast<int>(blockIdx.x), -2};
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -1540,6 +1544,28 @@ __global__ void k_zero_unwritten_y(uint16_t* __restrict__ Y, int slices, long lo
   }
 }
 
+// Zero the Y runs of the step-B pairs left out (see DeadY): one CTA per
+// pair in turn, one warp per row.
+__global__ void k_zero_dead_y(uint16_t* __restrict__ Y, int slices, long long slice_elems, long long ldk,
+                              int qrow, const DeadY* __restrict__ pairs, int n_pairs,
+                              const long long* __restrict__ seg, const int* __restrict__ n_ao, int s0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+    const DeadY e = pairs[p];
+    for (int q = warp; q < e.nq; q += nw) {
+      const int row = e.q0 + q;
+      if (row < 0 || row >= qrow) continue;
+      for (int a = e.a0; a < e.a1; ++a) {
+        const int na = n_ao[s0 + a];
+        const long long base = static_cast<long long>(row) * ldk + seg[a] + static_cast<long long>(e.aom) * na;
+        const int len = e.nm * na;
+        for (int i = lane; i < len; i += 32)
+          for (int sc = 0; sc < slices; ++sc) Y[sc * slice_elems + base + i] = 0;
+      }
+    }
+  }
+}
+
 // FP64 [rows][cols] (row stride ld), times scale -> 16-bit slices
 // [S][rows][kpad], zero for k >= cols
 __global__ void k_split_f64(const double* __restrict__ a, long long ld, int rows, int cols, int kpad,
@@ -1777,6 +1803,15 @@ void launch_zero_unwritten_y(void* Y, int slices, long long slice_elems, long lo
   tc::k_zero_unwritten_y<<<152 * 16, 256, 0, st>>>(static_cast<uint16_t*>(Y), slices, slice_elems, ldk,
                                                    Q0, qrow, ns, seg, n_ao, s0, ao_off, m0, m1, Lc, lo,
                                                    hi);
+}
+
+void launch_zero_dead_y(void* Y, int slices, long long slice_elems, long long ldk, int qrow,
+                        const DeadY* pairs, int n_pairs, const long long* seg, const int* n_ao, int s0,
+                        cudaStream_t st) {
+  if (n_pairs == 0) return;
+  const int grid = n_pairs < 152 * 8 ? n_pairs : 152 * 8;
+  tc::k_zero_dead_y<<<grid, 256, 0, st>>>(static_cast<uint16_t*>(Y), slices, slice_elems, ldk, qrow, pairs,
+                                          n_pairs, seg, n_ao, s0);
 }
 
 void launch_split_f64(const double* a, long long ld, int rows, int cols, int kpad, int slices,

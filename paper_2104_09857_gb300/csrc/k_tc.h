@@ -132,6 +132,18 @@ int launch_panel_tc_staged(int f16, float unscale, float out_scale, const CUtens
                            const int* atom_of_ao, const int* ao_off, const int* ri_off,
                            const int* n_ao, int npa, int pa0, int mu_base, int m_base, int nmc,
                            int flush_k, int* err_flag, cudaStream_t st);
+// A (row group, owner) pair of step B whose products are all zero: Y rows
+// [q0, q0 + nq) (batch-local), batch atoms [a0, a1), the owner's chunk-local
+// first AO aom and function count nm.
+struct DeadY {
+  int q0, nq, a0, a1, aom, nm;
+};
+// Zero, in both slices, the Y runs of the pairs: for each row and atom s of
+// the pair, Y[row][seg[s] + aom n(s), + nm n(s)) (seg per batch atom, n_ao
+// per atom, s0 the batch's first atom).
+void launch_zero_dead_y(void* Y, int slices, long long slice_elems, long long ldk, int qrow,
+                        const DeadY* pairs, int n_pairs, const long long* seg, const int* n_ao, int s0,
+                        cudaStream_t st);
 // Whether a mode-1 staged tile fits in the staging area: the owner has nm
 // functions and the tile's rows are the whole sigma-atoms with function
 // counts n_sig[0..count) (padding of every run taken at its worst).

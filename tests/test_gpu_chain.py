@@ -108,3 +108,32 @@ def test_ri_metric_matches_oracle(pkg):
         ref = och.apply_metric(s, ms[k])
         assert np.abs(got[k] - ref).max() <= 1e-11 * np.abs(ref).max()
     assert np.abs(same - ms[0]).max() <= 1e-14 * np.abs(ms[0]).max()
+
+
+def test_chain_at_the_benchmark_ri_size(pkg):
+    """The chain at the benchmark's RI size (298-atom ribbon, 7176 RI
+    functions): chi(i tau) of the timed FP16x3 form on 3 tau points feeds both
+    the GPU chain and the oracle chain; W^c(i tau) agree within 1e-10."""
+    import time
+
+    case = make_case("ribbon300", n_tau=3)
+    omega, gamma, delta, v, _, _ = chain_inputs(case)
+    with pkg.Context(0) as ctx:
+        ctx.load_case(case)
+        chi = ctx.chi_tau(case.thr, "fp16x3")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = ctx.chi_to_w(chi, v, gamma, delta)
+        torch.cuda.synchronize()
+        t_gpu = time.perf_counter() - t0
+        got = got.cpu().numpy()
+        chi_h = chi.cpu().numpy()
+        del chi
+    t0 = time.perf_counter()
+    ref, _ = och.chi_to_w(chi_h, v, gamma, delta)
+    t_cpu = time.perf_counter() - t0
+    errs = [_rel(got[j], ref[j]) for j in range(len(case.tau))]
+    print(f"chain, n_RI {chi_h.shape[1]}, {len(case.tau)} points: GPU {t_gpu:.2f} s, oracle {t_cpu:.1f} s, "
+          f"max rel error {max(errs):.2e}")
+    for j, e in enumerate(errs):
+        assert e <= TOL, f"tau {j}: {e:.3e}"
